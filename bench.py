@@ -1,0 +1,340 @@
+"""Benchmark of the SQ hot path on one GB300 (or N replicas under torchrun).
+
+Metric: SQ density throughput in grid points per second -- columns taken through the whole path in
+one step: Hamiltonian set-up (projector tables, spectral bounds), the K-step Chebyshev recursion of
+every column with moments and force moments, moment sums, Fermi level, weights, density, band
+energy/entropy and nonlocal forces.  Workload: the 95-atom mono-vacancy hcp Mg-like cell
+(48x42x59 grid = 118,944 points, 12th-order FD, s+p projectors, R_cut = 6 bohr -> 25^3 cubes,
+K = 60, kT = 0.005 Ha).  The main line is the FP32 recursion (FP64 Fermi solve and reductions); the
+FP64 recursion is measured in the same run under "fp64".
+
+  python bench.py [--steps K] [--warmup W] [--precision fp32|fp64|both] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2011_13517_gb300 import cells  # noqa: E402
+
+METRIC = "SQ density grid-points/sec (FP32 vs FP64) at stated rho error; % of roofline"
+UNIT = "grid-points/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 FMA roofline from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP64 roofline: the nominal GB300 FP64 rate (1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 1.25
+
+
+def workload_config(cell):
+    return {
+        "workload": (f"{cell.name}: hcp Mg-like mono-vacancy, {cell.n[0]}x{cell.n[1]}x{cell.n[2]} grid "
+                     f"({cell.N_d} points), {cell.fd_order}th-order FD, s+p KB projectors, "
+                     f"R_cut={cell.R_cut} bohr ({cell.n_c[0]}^3 cubes), K={cell.K}, kT={cell.kT} Ha"),
+        "grid_points": cell.N_d, "atoms": cell.natom, "K": cell.K, "cube": int(cell.n_c[0]),
+        "fd_order": cell.fd_order, "projectors_per_atom": 4,
+        "l2": "flushed (256 MiB write) between timed steps",
+        "data": "synthetic seeded hcp cell (Gaussian wells + smooth noise); stands in for the paper's "
+                "Troullier-Martins Mg systems",
+    }
+
+
+def algorithmic_flops(cell):
+    """FLOPs of one recursion-kernel launch counted from the method's definition: per column and
+    recursion step, the FD stencil (3 n_o + 1 FMAs per cube point) plus the Chebyshev update (1 FMA),
+    plus for each projector 2 |supp chi ^ C_q| FMAs (chi^T v and the rank-1 update); force moments
+    add 3 |supp ^ C_q| FMAs per projector of the atoms whose projectors are nonzero at x_q, at each of
+    the K+1 vectors.  FLOPs = 2 x FMAs."""
+    from oracle import oracle  # geometry of the projector supports (host-side counting only)
+    nc3 = int(np.prod(cell.n_c))
+    nproj = 1 if cell.lmax == 0 else 4
+    stencil = cell.K * nc3 * (3 * cell.fd_order + 2)
+    m = cell.m
+    # per atom, axis and window start s: overlap length of the support with [s, s + nc)
+    ov = []
+    inq = []
+    for J in range(cell.natom):
+        per_axis, per_axis_q = [], []
+        for a in range(3):
+            g = oracle.axis_factors(cell.R[J, a], cell.box[a], cell.n[a], cell.proj_sigma, cell.proj_rc)[0] != 0
+            n = int(cell.n[a])
+            nc = int(cell.n_c[a])
+            g2 = np.concatenate([g, g]).astype(np.int64)
+            cs = np.concatenate([[0], np.cumsum(g2)])
+            starts = (np.arange(n) - m[a]) % n            # window start of a column at index q_a
+            per_axis.append(cs[starts + nc] - cs[starts])
+            per_axis_q.append(g.astype(np.int64))
+        ov.append(per_axis)
+        inq.append(per_axis_q)
+    total_nl = 0
+    total_force = 0
+    for J in range(cell.natom):
+        ox, oy, oz = ov[J]
+        box = oz[:, None, None] * oy[None, :, None] * ox[None, None, :]
+        total_nl += int(box.sum())
+        qin = inq[J][2][:, None, None] * inq[J][1][None, :, None] * inq[J][0][None, None, :]
+        total_force += int((box * qin).sum())
+    fma = (cell.N_d * stencil + cell.K * 2 * nproj * total_nl + (cell.K + 1) * 3 * nproj * total_force)
+    return 2.0 * fma
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(cell, target_seconds=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of columns of the same workload."""
+    from oracle import oracle
+    lo, hi = oracle.spectral_bounds(cell)
+    omega, tau = oracle.scale_shift(lo, hi)
+    threads = oracle.max_threads()
+    rng = np.random.Generator(np.random.PCG64([23, 5]))
+    probe = rng.choice(cell.N_d, size=max(2 * threads, 8), replace=False)
+    t0 = time.perf_counter()
+    oracle.moments(cell, omega, tau, cols=probe, force=True)
+    per_col = (time.perf_counter() - t0) / probe.size
+    ncols = int(min(cell.N_d, max(probe.size, target_seconds / max(per_col, 1e-9))))
+    ncols = max(threads, (ncols // threads) * threads)
+    cols = rng.choice(cell.N_d, size=ncols, replace=False)
+    t0 = time.perf_counter()
+    oracle.moments(cell, omega, tau, cols=cols, force=True)
+    dt = time.perf_counter() - t0
+    return {"value": ncols / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{ncols} random columns of the {cell.N_d}-point workload (moments + force moments, "
+                      f"K={cell.K}); Fermi solve and observables are O(K M) per step and not sampled",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    cell = cells.vacancy_cell()
+    if rank != 0:
+        return
+    samples = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        base = cpu_baseline(cell, target_seconds=args.ref_seconds)
+        if i >= args.warmup:
+            samples.append(base["value"])
+    value = statistics.mean(samples)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * cell.N_d / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(cell),
+            "cpu_baseline": dict(base, value=value),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="both")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_2011_13517_gb300 import sq
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    cell = cells.vacancy_cell()
+    stream = torch.cuda.current_stream()
+    d_veff = torch.from_numpy(np.ascontiguousarray(cell.veff.reshape(-1))).cuda()
+    rho = torch.empty(cell.N_d, dtype=torch.float64, device="cuda")
+    force = torch.empty((cell.natom, 3), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def step(precision):
+        h = sq.build_for_cell(cell, d_veff=d_veff)
+        lam = sq.sq_density(h, cell.K, cell.kT, cell.N_e, precision, sq.SQ_WANT_FORCE, rho)
+        U, S, F = sq.sq_energy(h)
+        sq.sq_nonlocal_force(h, force)
+        timing = sq.sq_get_timing(h)
+        h.close()
+        return lam, U, S, timing
+
+    def measure(precision, steps, warmup):
+        for _ in range(warmup):
+            step(precision)
+        torch.cuda.synchronize()
+        times, rec = [], []
+        launches0 = sq.sq_kernel_launches()
+        res = None
+        with ClockSampler(local_rank) as clk:
+            for _ in range(steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                barrier()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = step(precision)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                barrier()
+                times.append(e0.elapsed_time(e1))
+                rec.append(res[3][0])
+        launches = (sq.sq_kernel_launches() - launches0) / steps
+        ms = statistics.mean(times)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, statistics.mean(rec), clk.summary(), launches, res
+
+    def measure_e2e(precision, steps):
+        """Through the public API with host buffers: V_eff from pinned host memory in, rho and forces
+        back to pinned host memory, all inside the timed region."""
+        host_veff = torch.from_numpy(np.ascontiguousarray(cell.veff.reshape(-1))).pin_memory()
+        host_rho = torch.empty(cell.N_d, dtype=torch.float64).pin_memory()
+        host_f = torch.empty((cell.natom, 3), dtype=torch.float64).pin_memory()
+        dv = torch.empty_like(d_veff)
+        times = []
+        for i in range(steps + 1):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dv.copy_(host_veff, non_blocking=True)
+            h = sq.build_for_cell(cell, d_veff=dv)
+            sq.sq_density(h, cell.K, cell.kT, cell.N_e, precision, sq.SQ_WANT_FORCE, rho)
+            sq.sq_energy(h)
+            sq.sq_nonlocal_force(h, force)
+            host_rho.copy_(rho, non_blocking=True)
+            host_f.copy_(force, non_blocking=True)
+            torch.cuda.synchronize()
+            h.close()
+            if i > 0:
+                times.append(time.perf_counter() - t0)
+        bi = cell.N_d * 8 + cell.natom * 3 * 8
+        bo = cell.N_d * 8 + cell.natom * 3 * 8
+        return cell.N_d / statistics.mean(times), bi, bo
+
+    flops = algorithmic_flops(cell)
+    results = {}
+    precs = ["fp32", "fp64"] if args.precision == "both" else [args.precision]
+    for p in precs:
+        code = sq.SQ_FP32 if p == "fp32" else sq.SQ_FP64
+        ms, rec_ms, clocks, launches, res = measure(code, args.steps, args.warmup)
+        peak = FP32_PEAK_TFLOPS if p == "fp32" else FP64_PEAK_TFLOPS
+        achieved = flops / (rec_ms * 1e-3) / 1e12
+        results[p] = dict(ms=ms, rec_ms=rec_ms, clocks=clocks, launches=launches, lam_f=res[0], U=res[1],
+                          S=res[2], value=world * cell.N_d / (ms * 1e-3),
+                          roofline={"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                    "frac": achieved / peak, "traffic": None,
+                                    "kernel": f"recursion_kernel<{'float' if p == 'fp32' else 'double'},6>",
+                                    "algorithmic_tflop_per_launch": flops / 1e12,
+                                    "kernel_ms": rec_ms,
+                                    "peak_source": ("FP32 unit count: 152 SM x 128 lanes x 2 x 2.07 GHz"
+                                                    if p == "fp32" else "nominal GB300 FP64 rate")})
+    main_p = precs[0]
+    m = results[main_p]
+    e2e_value, bi, bo = measure_e2e(sq.SQ_FP32 if main_p == "fp32" else sq.SQ_FP64, max(1, min(args.steps, 2)))
+    line = {
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if main_p == "fp32" else "f64", "data": "synthetic",
+        "config": dict(workload_config(cell), parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                       recursion_precision=main_p),
+        "roofline": m["roofline"], "clocks": m["clocks"], "gpu_launches": m["launches"],
+        "e2e": {"value": world * e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "results": {"lambda_f": m["lam_f"], "U": m["U"], "S": m["S"]},
+    }
+    for p in precs[1:]:
+        r = results[p]
+        line[p] = {"value": r["value"], "ms_per_step": r["ms"], "roofline": r["roofline"], "clocks": r["clocks"],
+                   "gpu_launches": r["launches"], "results": {"lambda_f": r["lam_f"], "U": r["U"], "S": r["S"]}}
+    if "fp32" in results and "fp64" in results:
+        line["fp32_vs_fp64"] = {"dlambda_f": abs(results["fp32"]["lam_f"] - results["fp64"]["lam_f"]),
+                                "dU_per_atom": abs(results["fp32"]["U"] - results["fp64"]["U"]) / cell.natom,
+                                "speedup": results["fp32"]["value"] / results["fp64"]["value"]}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cell)
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

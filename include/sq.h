@@ -1,0 +1,207 @@
+/*
+ * sq.h -- C ABI of libsq: Clenshaw-Curtis (Chebyshev) spectral quadrature on one GB300 (sm_103a).
+ *
+ * The library evaluates, for a given local effective potential V_eff on a periodic finite-difference
+ * grid and a set of atoms carrying Kleinman-Bylander projectors, the quantities of the linear-scaling
+ * spectral quadrature (SQ) method of Ghosh & Bhattacharya, arXiv 2011.13517:
+ *
+ *   - for every grid point q, the Chebyshev recursion of the Hamiltonian H_q truncated to the cube of
+ *     half-width R_cut around q (Sec. 3 "Hamiltonian at each grid point"; Eq. Chebyshev, Sec. 2.2),
+ *     started from the unit vector e_q, and its moments mu_k^q = e_q^T T_k(Hhat_q) e_q;
+ *   - the Fermi level from the electron-count constraint (Eq. Ne, Sec. 3), with the Chebyshev weights
+ *     of the Fermi-Dirac function (Eq. ChebyshevWeights, Eq. FermiDirac);
+ *   - the pointwise electron density (Eq. rhoq), the band energy U = 2 Tr(gamma H) and the electronic
+ *     entropy S (Eqs. uq, sq, RSIntegrals);
+ *   - the nonlocal atomic force from projector contractions of the same Chebyshev vectors
+ *     (Eq. NLforceSQ and the discrete nonlocal force of Sec. 3 "Atomic forces").
+ *
+ * Conventions for every entry point:
+ *   - Device buffers are caller-owned raw CUDA device pointers (allocated by e.g. PyTorch); host
+ *     buffers are plain host pointers.  The library owns only the workspace behind a handle.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work is
+ *     enqueued on that stream; entry points that return host scalars synchronise it.
+ *   - Grid arrays are [n3][n2][n1] with x (axis 0) fastest; point index q = i1 + n1 (i2 + n2 i3).
+ *   - Units: bohr and Hartree.  No exception or longjmp crosses the ABI.  A failing call returns a
+ *     nonzero sq_status, leaves caller outputs untouched, and sets a message for sq_last_error().
+ *   - One handle must not be used from two host threads at once.
+ */
+#ifndef SQ_H
+#define SQ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sq_handle_s *sq_handle;
+
+typedef enum {
+    SQ_OK = 0,
+    SQ_ERR_ARG = 1,               /* invalid argument (null pointer, bad size, bad flag)          */
+    SQ_ERR_CUBE_EXCEEDS_BOX = 2,  /* 2 round(R_cut/h_i) + 1 + n_o/2 > n_i on some axis            */
+    SQ_ERR_NO_BRACKET = 3,        /* N(lambda_min) > N_e or N(lambda_max) < N_e                    */
+    SQ_ERR_NOT_FINITE = 4,        /* V_eff, positions or a result is NaN/Inf                        */
+    SQ_ERR_CUDA = 5,              /* a CUDA runtime call failed (see sq_last_error)                 */
+    SQ_ERR_TIMEOUT = 6,           /* reserved: a bounded device wait gave up                        */
+    SQ_ERR_OOM = 7,               /* device allocation failed                                       */
+    SQ_ERR_STATE = 8,             /* call order: e.g. sq_energy before sq_density                   */
+    SQ_ERR_UNSUPPORTED = 9        /* e.g. FD order above 16, or too many atoms touching one cube    */
+} sq_status;
+
+/* precision of the Chebyshev recursion (moments, stencil sweeps, projector contractions).
+ * Moment sums, Chebyshev weights, the Fermi solve, rho, U, S and forces are always FP64. */
+enum { SQ_FP64 = 0, SQ_FP32 = 1 };
+
+/* flags of sq_density */
+enum { SQ_WANT_FORCE = 1 };
+
+/* Regular periodic grid (Sec. 3 "Discretization"): n_i points on [0, L_i), h_i = L_i / n_i, and the
+ * central finite-difference Laplacian of even order fd_order = n_o in {2, 4, ..., 16}. */
+typedef struct {
+    int n[3];
+    double L[3];
+    int fd_order;
+} sq_grid;
+
+/* Atoms and their Kleinman-Bylander projectors (Sec. 2.1, nonlocal operator
+ * V(x,x') = sum_J sum_lm c_Jl chi_Jlm(x) chi_Jlm(x')).  The projector shape is fixed by the library:
+ * with w(t) = exp(-t^2/(2 sigma^2)) (1 - t^2/rc^2)^3 for |t| < rc (0 otherwise) and
+ * N = (pi sigma^2)^(-3/4),
+ *     chi_s(x)   = N prod_i g_i(x_i - R_i),      g(t) = sum over periodic images of w,
+ *     chi_p_m(x) = sqrt(2)/sigma (x_m - R_m) chi_s(x)  (periodic-image sum of the same product),
+ * i.e. separable windowed Gaussians (a synthetic stand-in for the paper's Troullier-Martins
+ * projectors).  lmax = 0 uses chi_s only; lmax = 1 adds p_x, p_y, p_z.  The discrete operator is
+ * sum_J sum_lm c_l dV chi chi^T (dV = h1 h2 h3). */
+typedef struct {
+    int natom;                 /* >= 0 */
+    const double *R;           /* host [natom][3], bohr (any real values; wrapped periodically) */
+    int lmax;                  /* 0 or 1 */
+    double sigma;              /* > 0 */
+    double rc;                 /* > 0, window half-width */
+    const double *energy;      /* host [lmax+1] KB energies c_l (Ha) */
+} sq_atoms;
+
+/*
+ * sq_build_hamiltonian -- set up the discrete Kohn-Sham Hamiltonian (Sec. 2.1 Hamiltonian
+ * H = -1/2 Lap + V_eff + nonlocal; Sec. 3 "Discretization", "Hamiltonian at each grid point";
+ * Sec. 2.2 scale and shift).
+ *
+ *   grid        periodic grid and FD order (host struct, read during the call)
+ *   d_veff      device [N_d] FP64 V_eff, caller-owned; copied into the handle during the call
+ *   atoms       atoms and projector parameters (host struct and arrays, read during the call)
+ *   R_cut       half-width of the truncation cube (bohr); cube half-widths m_i = round(R_cut/h_i)
+ *               (ties to even).  Requires 2 m_i + 1 + fd_order/2 <= n_i on every axis, so that no
+ *               two cube points are stencil neighbours through the periodic wrap.
+ *   lambda_min, lambda_max
+ *               spectral bounds of H used for the scale and shift omega = (max+min)/2,
+ *               tau = (max-min)/2.  Pass NaN for both to let the library compute the rigorous bound
+ *               [min V + nl_lo, max kinetic eigenvalue + max V + nl_hi] (Weyl's inequality; the
+ *               nonlocal interval from Gershgorin row sums of the weighted projector Gram matrix).
+ *               Every truncated H_q is a principal submatrix of H, so the bound holds for all q.
+ *   stream      cudaStream_t (void*)
+ *   out         receives a new handle on success (free with sq_destroy)
+ * Errors: SQ_ERR_ARG, SQ_ERR_CUBE_EXCEEDS_BOX, SQ_ERR_NOT_FINITE, SQ_ERR_UNSUPPORTED, SQ_ERR_OOM,
+ * SQ_ERR_CUDA.  Synchronises `stream`.
+ */
+sq_status sq_build_hamiltonian(const sq_grid *grid, const double *d_veff, const sq_atoms *atoms,
+                               double R_cut, double lambda_min, double lambda_max, void *stream,
+                               sq_handle *out);
+
+/*
+ * sq_density -- the SQ hot path: per-point Chebyshev recursion (Eq. Chebyshev) of order K on the
+ * truncated scaled Hamiltonian, moments mu_k^q (k = 0..K), moment sums M_k = sum_q mu_k^q, the Fermi
+ * level (Eq. Ne) by bisection on [lambda_min, lambda_max], the Chebyshev weights c_k of the
+ * Fermi-Dirac function (Eq. ChebyshevWeights, M-point Chebyshev-Gauss quadrature with
+ * M = 2^ceil(log2 max(4(K+1), 16 tau/kT))), and the density rho(x_q) = 2 sum_k c_k mu_k^q / dV
+ * (Eq. rhoq; electrons per bohr^3, so sum_q rho dV = N_e).  With flags & SQ_WANT_FORCE it also
+ * accumulates the force moments A_k^{J,lm,d} = sum_q chi_Jlm(x_q) (d_d chi_Jlm)^T v_k^q used by
+ * sq_nonlocal_force (Eq. NLforceSQ).
+ *
+ *   h           handle from sq_build_hamiltonian
+ *   K           polynomial order, 1 <= K <= 4096
+ *   kT          smearing k_B theta (Ha), > 0
+ *   N_e         electron count, 0 < N_e < 2 N_d
+ *   precision   SQ_FP64 or SQ_FP32 (recursion precision)
+ *   flags       0 or SQ_WANT_FORCE
+ *   d_rho       device [N_d] FP64 output, caller-owned
+ *   lambda_f    host double output (Fermi level, Ha)
+ * Errors: SQ_ERR_ARG, SQ_ERR_NO_BRACKET, SQ_ERR_NOT_FINITE, SQ_ERR_OOM, SQ_ERR_CUDA.
+ * Synchronises `stream`.
+ */
+sq_status sq_density(sq_handle h, int K, double kT, double N_e, int precision, int flags,
+                     double *d_rho, double *lambda_f, void *stream);
+
+/*
+ * sq_fermi_level -- re-solve the electron-count equation (Eq. Ne) for a new kT / N_e from the
+ * moment sums stored by the last sq_density, and refresh the stored weights; d_rho (may be NULL)
+ * receives the matching density.  Same bisection rule as sq_density.
+ * Errors: SQ_ERR_STATE (no sq_density yet), SQ_ERR_ARG, SQ_ERR_NO_BRACKET, SQ_ERR_CUDA.
+ * Synchronises `stream`.
+ */
+sq_status sq_fermi_level(sq_handle h, double kT, double N_e, double *d_rho, double *lambda_f,
+                         void *stream);
+
+/*
+ * sq_energy -- band energy U = 2 Tr(gamma H) = 2 sum_k d_k M_k (d_k: Chebyshev weights of lam g),
+ * entropy S = -2 Tr s(H) = -2 sum_k e_k M_k (units of k_B, S >= 0; s = g ln g + (1-g) ln(1-g),
+ * Eq. FermiDirac and Eqs. uq, sq) and the band free energy F = U - kT S, at the Fermi level of the
+ * last sq_density / sq_fermi_level.  Host outputs (any may be NULL).
+ * Errors: SQ_ERR_STATE, SQ_ERR_CUDA.  Synchronises `stream`.
+ */
+sq_status sq_energy(sq_handle h, double *U, double *S, double *F, void *stream);
+
+/*
+ * sq_nonlocal_force -- nonlocal atomic forces f_J,d = 4 dV sum_lm c_l sum_k c_k A_k^{J,lm,d}
+ * (Eq. AtomicForce nonlocal term, Eq. NLforceSQ): the physical force -dF/dR_J of the KB energy,
+ * with the analytic gradient of the projectors.  Requires the last sq_density to have been called
+ * with SQ_WANT_FORCE.
+ *   d_force     device [natom][3] FP64 output, caller-owned
+ * Errors: SQ_ERR_STATE, SQ_ERR_ARG, SQ_ERR_CUDA.  Asynchronous on `stream`.
+ */
+sq_status sq_nonlocal_force(sq_handle h, double *d_force, void *stream);
+
+/* Spectral bounds in use (host outputs). */
+sq_status sq_get_spectral_bounds(sq_handle h, double *lambda_min, double *lambda_max);
+
+/*
+ * Read-only views of the last sq_density's results (library-owned, valid until the next
+ * sq_density or sq_destroy): d_mu is [K+1][N_d] in the recursion precision (float or double,
+ * see *precision), d_msum is [K+1] FP64 moment sums M_k.  Any output pointer may be NULL.
+ */
+sq_status sq_get_moments(sq_handle h, int *K, int *precision, const void **d_mu,
+                         const double **d_msum);
+
+/*
+ * sq_copy_moments -- copy the last sq_density's moments into caller-owned device buffers:
+ * d_mu [K+1][N_d] in the recursion precision (8 or 4 bytes per value) and d_msum [K+1] FP64.
+ * Either may be NULL.  Asynchronous on `stream`.
+ * Errors: SQ_ERR_STATE, SQ_ERR_CUDA.
+ */
+sq_status sq_copy_moments(sq_handle h, void *d_mu, double *d_msum, void *stream);
+
+/* Cube geometry in use: half-widths m[3] (grid points). */
+sq_status sq_get_cube(sq_handle h, int m[3]);
+
+/*
+ * sq_get_timing -- device time of the last sq_density's kernels, measured with CUDA events recorded
+ * on the caller's stream around them: the per-column recursion kernel alone, the moment sums, and
+ * the Fermi solve with weights and density (milliseconds; any output may be NULL).
+ */
+sq_status sq_get_timing(sq_handle h, double *recursion_ms, double *msum_ms, double *fermi_ms);
+
+/* Total number of kernels this library has launched in this process (for launch accounting). */
+long long sq_kernel_launches(void);
+
+/* Release a handle and its device workspace (NULL is ignored).  Synchronises the device. */
+void sq_destroy(sq_handle h);
+
+/* Static description of a status code. */
+const char *sq_status_string(sq_status s);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *sq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQ_H */

@@ -1,0 +1,1018 @@
+// libsq: C ABI entry points, set-up kernels (projector tables, bounds), moment sums, the Fermi-level
+// bisection and the observables.  The per-column recursion lives in sq_recursion.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "sq_internal.h"
+
+using namespace sq;
+
+// ------------------------------------------------------------------------------------------------
+// error reporting
+
+static thread_local char g_last_error[512] = "";
+
+static sq_status fail(sq_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define SQ_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? SQ_ERR_OOM : SQ_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                    \
+    } while (0)
+
+extern "C" const char *sq_last_error(void) { return g_last_error; }
+
+// number of kernels launched by this library (host-side count of launch sites executed)
+static long long g_launches = 0;
+#define SQ_COUNT(n) (g_launches += (n))
+
+extern "C" long long sq_kernel_launches(void) { return g_launches; }
+
+extern "C" const char *sq_status_string(sq_status s)
+{
+    switch (s) {
+    case SQ_OK: return "ok";
+    case SQ_ERR_ARG: return "invalid argument";
+    case SQ_ERR_CUBE_EXCEEDS_BOX: return "truncation cube plus stencil reach exceeds the periodic box";
+    case SQ_ERR_NO_BRACKET: return "electron count not bracketed by the spectral bounds";
+    case SQ_ERR_NOT_FINITE: return "non-finite input or result";
+    case SQ_ERR_CUDA: return "CUDA runtime error";
+    case SQ_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SQ_ERR_OOM: return "device allocation failed";
+    case SQ_ERR_STATE: return "call made in the wrong state";
+    case SQ_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+// ------------------------------------------------------------------------------------------------
+// handle
+
+struct sq_handle_s {
+    int dev = 0;
+    int num_sms = 0;
+    int n[3] = {0, 0, 0};
+    double L[3] = {0, 0, 0}, h[3] = {0, 0, 0}, dV = 0;
+    int fd_order = 0, p = 0;
+    double fd[kMaxHalfWidth + 1] = {0};
+    int m[3] = {0, 0, 0}, nc[3] = {0, 0, 0};
+    long long N_d = 0;
+    int nc3 = 0;
+    int natom = 0, lmax = 0, nproj = 1;
+    double sigma = 0, rc = 0, cl[2] = {0, 0}, Nnorm = 0;
+    double lmin = 0, lmax_ = 0, omega = 0, tau = 0, kdiag = 0;
+    // device set-up data
+    double *d_veff = nullptr;       // [N_d]
+    double *d_fac64 = nullptr;      // [natom][3][4][n_a]
+    double *d_fac2_64 = nullptr;    // doubled FP64 tables
+    float *d_fac2_32 = nullptr;     // doubled FP32 tables
+    int *d_sup = nullptr;           // [natom][3] start, then [natom][3] len
+    int fac64_off[3] = {0, 0, 0}, fac64_stride = 0;
+    int fac2_off[3] = {0, 0, 0}, fac2_stride = 0;
+    double *d_dpad64 = nullptr;
+    float *d_dpad32 = nullptr;
+    int pn[3] = {0, 0, 0};
+    double *d_small = nullptr;      // small scratch: reductions, bisection state
+    // density state
+    int have_density = 0, K = 0, precision = 0, have_force = 0;
+    double kT = 0, N_e = 0, lam_f = 0;
+    int M = 0;
+    void *d_mu = nullptr;
+    size_t mu_bytes = 0;
+    double *d_msum = nullptr, *d_msum_part = nullptr;
+    size_t msum_cap = 0, part_cap = 0;
+    double *d_A = nullptr;
+    size_t A_cap = 0;
+    double *d_coef = nullptr;       // [3][K+1]: c, d, e
+    size_t coef_cap = 0;
+    double *d_nodes = nullptr;      // [3][M]: lambda_j, D_j, scratch f_j
+    size_t nodes_cap = 0;
+    void *d_scratch = nullptr;      // per-CTA vectors when not in shared memory
+    size_t scratch_cap = 0;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    float t_rec = 0, t_msum = 0, t_fermi = 0;
+};
+
+template <typename P>
+static sq_status ensure(P **ptr, size_t *cap, size_t bytes)
+{
+    if (*cap >= bytes && *ptr) return SQ_OK;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc((void **)ptr, bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess) return fail(SQ_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    *cap = bytes;
+    return SQ_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// set-up kernels
+
+// Periodised 1D projector factors g, hp, g', hp' of atom J on axis a at grid index i (FP64).
+__global__ void k_factors(int natom, const double *R, double L0, double L1, double L2, int n0, int n1, int n2,
+                          double sigma, double rc, double *fac64, int stride, int off0, int off1, int off2)
+{
+    const int n[3] = {n0, n1, n2};
+    const double Lx[3] = {L0, L1, L2};
+    const int off[3] = {off0, off1, off2};
+    const int total = n0 + n1 + n2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)natom * total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int J = (int)(t / total);
+        int r = (int)(t % total);
+        int a = 0;
+        while (r >= n[a]) {
+            r -= n[a];
+            a++;
+        }
+        const int i = r;
+        const double La = Lx[a];
+        const double h = La / n[a];
+        const double x = i * h;
+        const double Ra = R[3 * J + a];
+        const double pf = sqrt(2.0) / sigma;
+        double sg = 0, sh = 0, sgd = 0, shd = 0;
+        const int lo = (int)floor((x - Ra - rc) / La) - 1;
+        const int hi = (int)ceil((x - Ra + rc) / La) + 1;
+        for (int im = lo; im <= hi; im++) {
+            const double tt = x - Ra - im * La;
+            if (fabs(tt) >= rc) continue;
+            const double u = 1.0 - tt * tt / (rc * rc);
+            const double e = exp(-tt * tt / (2.0 * sigma * sigma));
+            const double w = e * u * u * u;
+            const double wd = e * (-tt / (sigma * sigma) * u * u * u - 6.0 * tt / (rc * rc) * u * u);
+            sg += w;
+            sgd += wd;
+            sh += pf * tt * w;
+            shd += pf * (w + tt * wd);
+        }
+        double *base = fac64 + (size_t)J * stride + off[a];
+        base[0 * n[a] + i] = sg;
+        base[1 * n[a] + i] = sh;
+        base[2 * n[a] + i] = sgd;
+        base[3 * n[a] + i] = shd;
+    }
+}
+
+// Support (periodic interval where g != 0) of atom J on axis a: start and length.
+__global__ void k_support(int natom, const double *fac64, int stride, int off0, int off1, int off2, int n0,
+                          int n1, int n2, int *sup, int *bad)
+{
+    const int n[3] = {n0, n1, n2};
+    const int off[3] = {off0, off1, off2};
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < natom * 3; t += gridDim.x * blockDim.x) {
+        const int J = t / 3, a = t % 3;
+        const double *g = fac64 + (size_t)J * stride + off[a];
+        int cnt = 0, starts = 0, st = 0;
+        for (int i = 0; i < n[a]; i++) {
+            const bool on = g[i] != 0.0;
+            const bool prev = g[(i + n[a] - 1) % n[a]] != 0.0;
+            cnt += on;
+            if (on && !prev) {
+                starts++;
+                st = i;
+            }
+        }
+        if (cnt == n[a]) st = 0;
+        else if (starts != 1) atomicExch(bad, 1);
+        sup[J * 3 + a] = st;
+        sup[natom * 3 + J * 3 + a] = cnt;
+    }
+}
+
+// Doubled tables in precision T: element (J, a, f, i), i < 2 n_a, = fac64(J, a, f, i mod n_a).
+template <typename T>
+__global__ void k_double_tables(int natom, const double *fac64, int s64, int o0, int o1, int o2, int n0, int n1,
+                                int n2, T *fac2, int s2, int p0, int p1, int p2)
+{
+    const int n[3] = {n0, n1, n2};
+    const int o64[3] = {o0, o1, o2};
+    const int o2x[3] = {p0, p1, p2};
+    const int per = 2 * kNumFactors * (n0 + n1 + n2);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)natom * per;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int J = (int)(t / per);
+        int r = (int)(t % per);
+        int a = 0;
+        while (r >= 2 * kNumFactors * n[a]) {
+            r -= 2 * kNumFactors * n[a];
+            a++;
+        }
+        const int f = r / (2 * n[a]);
+        const int i = r % (2 * n[a]);
+        fac2[(size_t)J * s2 + o2x[a] + f * 2 * n[a] + i] =
+            (T)fac64[(size_t)J * s64 + o64[a] + f * n[a] + (i % n[a])];
+    }
+}
+
+// min and max of V_eff, and a non-finite flag; out[0] = min, out[1] = max (as ordered bit patterns)
+__global__ void k_vrange(const double *v, long long n, unsigned long long *mn, unsigned long long *mx, int *bad)
+{
+    double lo = INFINITY, hi = -INFINITY;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double x = v[i];
+        if (!isfinite(x)) atomicExch(bad, 1);
+        lo = fmin(lo, x);
+        hi = fmax(hi, x);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        // order-preserving map of doubles onto unsigned integers
+        auto key = [](double d) {
+            unsigned long long b = (unsigned long long)__double_as_longlong(d);
+            return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+        };
+        atomicMin(mn, key(lo));
+        atomicMax(mx, key(hi));
+    }
+}
+
+// Gershgorin bound of the weighted projector Gram matrix: max_P sum_P' sqrt|c_P c_P'| dV |<chi_P, chi_P'>|
+__global__ void k_gram_bound(int natom, int nproj, const double *fac64, int stride, int o0, int o1, int o2,
+                             int n0, int n1, int n2, double c0, double c1, double scale, unsigned long long *out)
+{
+    const int n[3] = {n0, n1, n2};
+    const int off[3] = {o0, o1, o2};
+    const int P = blockIdx.x;
+    if (P >= natom * nproj) return;
+    const int J = P / nproj, lm = P % nproj;
+    const double cP = fabs(lm == 0 ? c0 : c1);
+    double row = 0.0;
+    for (int Q = threadIdx.x; Q < natom * nproj; Q += blockDim.x) {
+        const int J2 = Q / nproj, lm2 = Q % nproj;
+        const double cQ = fabs(lm2 == 0 ? c0 : c1);
+        double prod = 1.0;
+        for (int a = 0; a < 3; a++) {
+            const double *f1 = fac64 + (size_t)J * stride + off[a] + (lm == 1 + a ? 1 : 0) * n[a];
+            const double *f2 = fac64 + (size_t)J2 * stride + off[a] + (lm2 == 1 + a ? 1 : 0) * n[a];
+            double s = 0.0;
+            for (int i = 0; i < n[a]; i++) s += f1[i] * f2[i];
+            prod *= s;
+        }
+        row += sqrt(cP * cQ) * fabs(prod);
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) row += __shfl_xor_sync(0xffffffffu, row, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = row;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+        atomicMax(out, (unsigned long long)__double_as_longlong(s * scale));  // s >= 0
+    }
+}
+
+// Hhat diagonal on the padded grid: (kdiag + V(g) - omega)/tau, g = padded index - m (periodic)
+template <typename T>
+__global__ void k_dpad(const double *veff, int n0, int n1, int n2, int m0, int m1, int m2, double kdiag,
+                       double omega, double tau, T *dpad)
+{
+    const int p0 = n0 + 2 * m0, p1 = n1 + 2 * m1, p2 = n2 + 2 * m2;
+    const long long tot = (long long)p0 * p1 * p2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % p0);
+        const int j = (int)((t / p0) % p1);
+        const int k = (int)(t / ((long long)p0 * p1));
+        const int g0 = ((i - m0) % n0 + n0) % n0;
+        const int g1 = ((j - m1) % n1 + n1) % n1;
+        const int g2 = ((k - m2) % n2 + n2) % n2;
+        const double v = veff[g0 + (long long)n0 * (g1 + (long long)n1 * g2)];
+        dpad[t] = (T)((kdiag + v - omega) / tau);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// moment sums M_k = sum_q mu_k^q (FP64, deterministic two-stage reduction)
+
+constexpr int kSumBlocks = 64;
+
+template <typename T>
+__global__ void k_msum_partial(const T *mu, long long N_d, int K, double *part)
+{
+    const int k = blockIdx.y;
+    double s = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N_d; q += (long long)gridDim.x * blockDim.x)
+        s += (double)mu[(size_t)k * N_d + q];
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        part[(size_t)k * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+__global__ void k_msum_final(const double *part, int nblk, int K, double *msum, int *bad)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; b++) s += part[(size_t)k * nblk + b];
+        if (!isfinite(s)) atomicExch(bad, 1);
+        msum[k] = s;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Fermi level.  Nodes x_j = cos(theta_j), theta_j = pi (j + 1/2)/M;
+// D_j = sum_k (2 - delta_k0)/M M_k cos(k theta_j), so that N(lambda_f) = 2 sum_k c_k M_k
+// = 2 sum_j g(tau x_j + omega; lambda_f) D_j.
+
+__device__ __forceinline__ double cos_k_theta(int k, int j, int M)
+{
+    // cos(k pi (2j+1)/(2M)) with exact argument reduction modulo 2 pi
+    const long long r = ((long long)k * (2LL * j + 1)) % (4LL * M);
+    return cospi((double)r / (2.0 * M));
+}
+
+__device__ __forceinline__ double fermi_fn(double lam, double lam_f, double kT)
+{
+    return 0.5 * (1.0 - tanh((lam - lam_f) / (2.0 * kT)));
+}
+
+__global__ void k_nodes(const double *msum, int K, int M, double omega, double tau, double *lam, double *D)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+        lam[j] = tau * cospi((j + 0.5) / M) + omega;
+        double s = msum[0];
+        for (int k = 1; k <= K; k++) s += 2.0 * msum[k] * cos_k_theta(k, j, M);
+        D[j] = s / M;
+    }
+}
+
+struct FermiState {
+    double lo, hi;        // bracket
+    double x;             // current evaluation point
+    double N_lo, N_hi;    // values at the bracket ends (diagnostics)
+    int phase;            // 0: evaluate at lo, 1: at hi, 2: bisecting, 3: done, 4: no bracket
+    int iter;
+    unsigned int arrived; // last-block counter
+    int pad;
+};
+
+constexpr int kFermiBlocks = 96;
+
+// One bisection step: all blocks sum 2 g(lam_j) D_j at the state's point; the last block to finish
+// reduces the per-block partials in fixed order and advances the state.  Sequence:
+// phase 0 evaluates N(lo), phase 1 N(hi) (bracket check), phase 2 bisects
+// (mid = lo + (hi-lo)/2; N(mid) < N_e -> lo = mid else hi = mid) until the midpoint no longer
+// separates the bracket.
+__global__ void k_fermi_step(const double *lam, const double *D, int M, double kT, double N_e, FermiState *st,
+                             double *part)
+{
+    __shared__ double red[32];
+    __shared__ bool last;
+    const int phase = st->phase;
+    if (phase >= 3) return;
+    double x;
+    if (phase == 0) x = st->lo;
+    else if (phase == 1) x = st->hi;
+    else x = st->lo + 0.5 * (st->hi - st->lo);
+    double s = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x)
+        s += fermi_fn(lam[j], x, kT) * D[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        part[blockIdx.x] = t;
+        __threadfence();
+        const unsigned int prev = atomicAdd(&st->arrived, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double N = 0.0;
+    for (int b = 0; b < (int)gridDim.x; b++) N += ((volatile double *)part)[b];
+    N *= 2.0;
+    st->arrived = 0;
+    if (phase == 0) {
+        st->N_lo = N;
+        st->phase = (N > N_e) ? 4 : 1;
+    } else if (phase == 1) {
+        st->N_hi = N;
+        st->phase = (N < N_e) ? 4 : 2;
+    } else {
+        if (N < N_e) st->lo = x;
+        else st->hi = x;
+        st->iter++;
+        const double nm = st->lo + 0.5 * (st->hi - st->lo);
+        if (nm <= st->lo || nm >= st->hi || st->iter >= 200) {
+            st->x = nm;
+            st->phase = 3;
+        }
+    }
+}
+
+// f_j for the three expansions: g, lam g, s(g) at the Fermi level
+__global__ void k_node_functions(const double *lam, int M, double lam_f, double kT, double *fg, double *flg,
+                                 double *fs)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+        const double l = lam[j];
+        const double g = fermi_fn(l, lam_f, kT);
+        const double y = fabs((l - lam_f) / kT);
+        fg[j] = g;
+        flg[j] = l * g;
+        fs[j] = -(log1p(exp(-y)) + y * fermi_fn(y, 0.0, 1.0));
+    }
+}
+
+// a_k = (2 - delta_k0)/M sum_j f_j cos(k theta_j) for the three functions (block per (k, function))
+__global__ void k_coeffs(const double *f0, const double *f1, const double *f2, int M, int K, double *coef)
+{
+    const int k = blockIdx.x, which = blockIdx.y;
+    const double *f = which == 0 ? f0 : (which == 1 ? f1 : f2);
+    double s = 0.0;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) s += f[j] * cos_k_theta(k, j, M);
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        coef[which * (K + 1) + k] = t * (k == 0 ? 1.0 : 2.0) / M;
+    }
+}
+
+// rho(x_q) = 2 sum_k c_k mu_k^q / dV
+template <typename T>
+__global__ void k_density(const T *mu, long long N_d, int K, const double *c, double inv_dV, double *rho)
+{
+    __shared__ double cs[512];
+    for (int k = threadIdx.x; k <= K && k < 512; k += blockDim.x) cs[k] = c[k];
+    __syncthreads();
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N_d; q += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k <= K; k++) s += (k < 512 ? cs[k] : c[k]) * (double)mu[(size_t)k * N_d + q];
+        rho[q] = 2.0 * s * inv_dV;
+    }
+}
+
+// U = 2 sum d_k M_k, S = -2 sum e_k M_k
+__global__ void k_energy(const double *msum, const double *coef, int K, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double U = 0.0, S = 0.0;
+    for (int k = 0; k <= K; k++) {
+        U += coef[(K + 1) + k] * msum[k];
+        S += coef[2 * (K + 1) + k] * msum[k];
+    }
+    out[0] = 2.0 * U;
+    out[1] = -2.0 * S;
+}
+
+// f_J,d = 4 dV sum_lm c_l sum_k c_k A_k^{J,lm,d}
+__global__ void k_force(const double *A, const double *c, int K, int natom, int nproj, double c0, double c1,
+                        double dV, double *force)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < natom * 3; t += gridDim.x * blockDim.x) {
+        const int J = t / 3, d = t % 3;
+        double f = 0.0;
+        for (int lm = 0; lm < nproj; lm++) {
+            double s = 0.0;
+            for (int k = 0; k <= K; k++) s += c[k] * A[(((size_t)k * natom + J) * nproj + lm) * 3 + d];
+            f += (lm == 0 ? c0 : c1) * s;
+        }
+        force[t] = 4.0 * dV * f;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// host helpers
+
+static void fd_coefficients(int order, double *c)
+{
+    // central second-derivative weights: c_j = 2 (-1)^(j+1) (p!)^2 / (j^2 (p-j)! (p+j)!)
+    const int p = order / 2;
+    double sum = 0.0;
+    for (int j = 1; j <= p; j++) {
+        double r = 1.0;
+        for (int i = 1; i <= j; i++) r *= (double)(p - j + i) / (double)(p + i);
+        c[j] = 2.0 * ((j % 2) ? 1.0 : -1.0) * r / ((double)j * j);
+        sum += c[j];
+    }
+    c[0] = -2.0 * sum;
+}
+
+static double kinetic_max(const sq_handle_s *h)
+{
+    // eigenvalues of -1/2 Lap_h on the periodic grid: sum_i -(c_0 + 2 sum_j c_j cos(j theta)) / (2 h_i^2)
+    double tot = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double best = -INFINITY;
+        for (int k = 0; k < h->n[a]; k++) {
+            const double th = 2.0 * M_PI * k / h->n[a];
+            double s = h->fd[0];
+            for (int j = 1; j <= h->p; j++) s += 2.0 * h->fd[j] * cos(j * th);
+            best = fmax(best, -s / (2.0 * h->h[a] * h->h[a]));
+        }
+        tot += best;
+    }
+    return tot;
+}
+
+static double key_to_double(unsigned long long k)
+{
+    unsigned long long b = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+    double d;
+    memcpy(&d, &b, sizeof(d));
+    return d;
+}
+
+static int grid_for(long long work, int block, int num_sms)
+{
+    long long g = (work + block - 1) / block;
+    long long cap = (long long)num_sms * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// ------------------------------------------------------------------------------------------------
+// ABI
+
+extern "C" sq_status sq_build_hamiltonian(const sq_grid *grid, const double *d_veff, const sq_atoms *atoms,
+                                          double R_cut, double lambda_min, double lambda_max, void *stream_,
+                                          sq_handle *out)
+{
+    g_last_error[0] = 0;
+    if (!grid || !d_veff || !atoms || !out) return fail(SQ_ERR_ARG, "null argument");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    for (int a = 0; a < 3; a++)
+        if (grid->n[a] < 1 || !(grid->L[a] > 0) || !std::isfinite(grid->L[a]))
+            return fail(SQ_ERR_ARG, "grid axis %d: n=%d L=%g", a, grid->n[a], grid->L[a]);
+    if (grid->fd_order < 2 || grid->fd_order % 2 || grid->fd_order / 2 > kMaxHalfWidth)
+        return fail(grid->fd_order > 2 * kMaxHalfWidth ? SQ_ERR_UNSUPPORTED : SQ_ERR_ARG, "fd_order %d", grid->fd_order);
+    if (atoms->natom < 0 || (atoms->natom > 0 && !atoms->R) || (atoms->lmax != 0 && atoms->lmax != 1) ||
+        !(atoms->sigma > 0) || !(atoms->rc > 0) || !atoms->energy)
+        return fail(SQ_ERR_ARG, "atoms: natom=%d lmax=%d sigma=%g rc=%g", atoms->natom, atoms->lmax, atoms->sigma,
+                    atoms->rc);
+    if (!(R_cut >= 0) || !std::isfinite(R_cut)) return fail(SQ_ERR_ARG, "R_cut %g", R_cut);
+    for (int i = 0; i < 3 * atoms->natom; i++)
+        if (!std::isfinite(atoms->R[i])) return fail(SQ_ERR_NOT_FINITE, "atom position %d", i);
+    const bool want_bounds = std::isnan(lambda_min) || std::isnan(lambda_max);
+    if (!want_bounds && !(lambda_max > lambda_min)) return fail(SQ_ERR_ARG, "lambda_max <= lambda_min");
+
+    sq_handle_s *h = new sq_handle_s();
+    auto cleanup = [&](sq_status s) {
+        sq_destroy(h);
+        return s;
+    };
+    if (cudaGetDevice(&h->dev) != cudaSuccess) return cleanup(fail(SQ_ERR_CUDA, "no CUDA device"));
+    for (int i = 0; i < 5; i++) SQ_CUDA(cudaEventCreate(&h->ev[i]));
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev);
+    h->fd_order = grid->fd_order;
+    h->p = grid->fd_order / 2;
+    fd_coefficients(h->fd_order, h->fd);
+    h->N_d = 1;
+    h->dV = 1.0;
+    h->kdiag = 0.0;
+    for (int a = 0; a < 3; a++) {
+        h->n[a] = grid->n[a];
+        h->L[a] = grid->L[a];
+        h->h[a] = grid->L[a] / grid->n[a];
+        h->dV *= h->h[a];
+        h->N_d *= grid->n[a];
+        h->m[a] = (int)std::nearbyint(R_cut / h->h[a]);
+        h->nc[a] = 2 * h->m[a] + 1;
+        h->kdiag += -h->fd[0] / (2.0 * h->h[a] * h->h[a]);
+        if (h->nc[a] + h->p > h->n[a])
+            return cleanup(fail(SQ_ERR_CUBE_EXCEEDS_BOX, "axis %d: 2m+1+p = %d > n = %d", a, h->nc[a] + h->p, h->n[a]));
+        h->pn[a] = h->n[a] + 2 * h->m[a];
+    }
+    h->nc3 = h->nc[0] * h->nc[1] * h->nc[2];
+    h->natom = atoms->natom;
+    h->lmax = atoms->lmax;
+    h->nproj = atoms->lmax == 0 ? 1 : 4;
+    h->sigma = atoms->sigma;
+    h->rc = atoms->rc;
+    h->cl[0] = atoms->energy[0];
+    h->cl[1] = atoms->lmax ? atoms->energy[1] : 0.0;
+    if (!std::isfinite(h->cl[0]) || !std::isfinite(h->cl[1])) return cleanup(fail(SQ_ERR_NOT_FINITE, "KB energy"));
+    h->Nnorm = pow(M_PI * h->sigma * h->sigma, -0.75);
+
+    size_t cap = 0;
+    sq_status s;
+    if ((s = ensure(&h->d_veff, &cap, sizeof(double) * h->N_d))) return cleanup(s);
+    SQ_CUDA(cudaMemcpyAsync(h->d_veff, d_veff, sizeof(double) * h->N_d, cudaMemcpyDeviceToDevice, stream));
+
+    // projector tables
+    h->fac64_off[0] = 0;
+    h->fac64_off[1] = kNumFactors * h->n[0];
+    h->fac64_off[2] = kNumFactors * (h->n[0] + h->n[1]);
+    h->fac64_stride = kNumFactors * (h->n[0] + h->n[1] + h->n[2]);
+    h->fac2_off[0] = 0;
+    h->fac2_off[1] = 2 * kNumFactors * h->n[0];
+    h->fac2_off[2] = 2 * kNumFactors * (h->n[0] + h->n[1]);
+    h->fac2_stride = 2 * kNumFactors * (h->n[0] + h->n[1] + h->n[2]);
+    const int na = h->natom > 0 ? h->natom : 1;
+    double *d_R = nullptr;
+    cap = 0;
+    if ((s = ensure(&h->d_fac64, &cap, sizeof(double) * (size_t)na * h->fac64_stride))) return cleanup(s);
+    cap = 0;
+    if ((s = ensure(&h->d_fac2_64, &cap, sizeof(double) * (size_t)na * h->fac2_stride))) return cleanup(s);
+    cap = 0;
+    if ((s = ensure(&h->d_fac2_32, &cap, sizeof(float) * (size_t)na * h->fac2_stride))) return cleanup(s);
+    cap = 0;
+    if ((s = ensure(&h->d_sup, &cap, sizeof(int) * 6 * (size_t)na))) return cleanup(s);
+    cap = 0;
+    if ((s = ensure(&h->d_small, &cap, 4096))) return cleanup(s);
+    SQ_CUDA(cudaMemsetAsync(h->d_small, 0, 4096, stream));
+    int *d_bad = reinterpret_cast<int *>(h->d_small);
+    unsigned long long *d_keys = reinterpret_cast<unsigned long long *>(h->d_small) + 8;
+    if (h->natom > 0) {
+        SQ_CUDA(cudaMalloc(&d_R, sizeof(double) * 3 * h->natom));
+        SQ_CUDA(cudaMemcpyAsync(d_R, atoms->R, sizeof(double) * 3 * h->natom, cudaMemcpyHostToDevice, stream));
+        const long long work = (long long)h->natom * (h->n[0] + h->n[1] + h->n[2]);
+        SQ_COUNT(1);
+        k_factors<<<grid_for(work, 256, h->num_sms), 256, 0, stream>>>(
+            h->natom, d_R, h->L[0], h->L[1], h->L[2], h->n[0], h->n[1], h->n[2], h->sigma, h->rc, h->d_fac64,
+            h->fac64_stride, h->fac64_off[0], h->fac64_off[1], h->fac64_off[2]);
+        SQ_CUDA(cudaGetLastError());
+        SQ_COUNT(1);
+        k_support<<<grid_for(3LL * h->natom, 128, h->num_sms), 128, 0, stream>>>(
+            h->natom, h->d_fac64, h->fac64_stride, h->fac64_off[0], h->fac64_off[1], h->fac64_off[2], h->n[0],
+            h->n[1], h->n[2], h->d_sup, d_bad + 1);
+        SQ_CUDA(cudaGetLastError());
+        const long long work2 = (long long)h->natom * h->fac2_stride;
+        SQ_COUNT(2);
+        k_double_tables<double><<<grid_for(work2, 256, h->num_sms), 256, 0, stream>>>(
+            h->natom, h->d_fac64, h->fac64_stride, h->fac64_off[0], h->fac64_off[1], h->fac64_off[2], h->n[0],
+            h->n[1], h->n[2], h->d_fac2_64, h->fac2_stride, h->fac2_off[0], h->fac2_off[1], h->fac2_off[2]);
+        SQ_CUDA(cudaGetLastError());
+        k_double_tables<float><<<grid_for(work2, 256, h->num_sms), 256, 0, stream>>>(
+            h->natom, h->d_fac64, h->fac64_stride, h->fac64_off[0], h->fac64_off[1], h->fac64_off[2], h->n[0],
+            h->n[1], h->n[2], h->d_fac2_32, h->fac2_stride, h->fac2_off[0], h->fac2_off[1], h->fac2_off[2]);
+        SQ_CUDA(cudaGetLastError());
+    }
+    // V_eff range and finiteness
+    {
+        unsigned long long init[2] = {~0ull, 0ull};
+        SQ_CUDA(cudaMemcpyAsync(d_keys, init, sizeof(init), cudaMemcpyHostToDevice, stream));
+        SQ_COUNT(1);
+        k_vrange<<<grid_for(h->N_d, 256, h->num_sms), 256, 0, stream>>>(h->d_veff, h->N_d, d_keys, d_keys + 1, d_bad);
+        SQ_CUDA(cudaGetLastError());
+    }
+    if (want_bounds && h->natom > 0) {
+        const double scale = h->dV * h->Nnorm * h->Nnorm;
+        SQ_COUNT(1);
+        k_gram_bound<<<h->natom * h->nproj, 256, 0, stream>>>(
+            h->natom, h->nproj, h->d_fac64, h->fac64_stride, h->fac64_off[0], h->fac64_off[1], h->fac64_off[2],
+            h->n[0], h->n[1], h->n[2], h->cl[0], h->cl[1], scale, d_keys + 2);
+        SQ_CUDA(cudaGetLastError());
+    }
+    int bad[2];
+    unsigned long long keys[3];
+    SQ_CUDA(cudaMemcpyAsync(bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, stream));
+    SQ_CUDA(cudaMemcpyAsync(keys, d_keys, sizeof(keys), cudaMemcpyDeviceToHost, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    if (d_R) cudaFree(d_R);
+    if (bad[0]) return cleanup(fail(SQ_ERR_NOT_FINITE, "V_eff has non-finite values"));
+    if (bad[1]) return cleanup(fail(SQ_ERR_ARG, "projector support is not a periodic interval"));
+    if (want_bounds) {
+        const double vmin = key_to_double(keys[0]), vmax = key_to_double(keys[1]);
+        double nl = 0.0;
+        if (h->natom > 0) memcpy(&nl, &keys[2], sizeof(nl));
+        const bool cpos = h->cl[0] >= 0 && (h->nproj == 1 || h->cl[1] >= 0);
+        const bool cneg = h->cl[0] <= 0 && (h->nproj == 1 || h->cl[1] <= 0);
+        const double nlo = cpos ? 0.0 : -nl, nhi = cneg ? 0.0 : nl;
+        h->lmin = vmin + nlo;
+        h->lmax_ = kinetic_max(h) + vmax + nhi;
+    } else {
+        h->lmin = lambda_min;
+        h->lmax_ = lambda_max;
+    }
+    h->omega = 0.5 * (h->lmax_ + h->lmin);
+    h->tau = 0.5 * (h->lmax_ - h->lmin);
+    *out = h;
+    return SQ_OK;
+}
+
+extern "C" void sq_destroy(sq_handle h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    cudaFree(h->d_veff);
+    cudaFree(h->d_fac64);
+    cudaFree(h->d_fac2_64);
+    cudaFree(h->d_fac2_32);
+    cudaFree(h->d_sup);
+    cudaFree(h->d_dpad64);
+    cudaFree(h->d_dpad32);
+    cudaFree(h->d_small);
+    cudaFree(h->d_mu);
+    cudaFree(h->d_msum);
+    cudaFree(h->d_msum_part);
+    cudaFree(h->d_A);
+    cudaFree(h->d_coef);
+    cudaFree(h->d_nodes);
+    cudaFree(h->d_scratch);
+    for (int i = 0; i < 5; i++)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    delete h;
+}
+
+template <typename T>
+static sq_status run_recursion(sq_handle h, int K, int want_force, cudaStream_t stream)
+{
+    sq_status s;
+    const size_t pad = (size_t)h->pn[0] * h->pn[1] * h->pn[2];
+    T **dpad = nullptr;
+    if constexpr (sizeof(T) == 8) dpad = reinterpret_cast<T **>(&h->d_dpad64);
+    else dpad = reinterpret_cast<T **>(&h->d_dpad32);
+    if (!*dpad) {
+        size_t cap = 0;
+        if ((s = ensure(dpad, &cap, sizeof(T) * pad))) return s;
+    }
+    SQ_COUNT(1);
+    k_dpad<T><<<grid_for((long long)pad, 256, h->num_sms), 256, 0, stream>>>(
+        h->d_veff, h->n[0], h->n[1], h->n[2], h->m[0], h->m[1], h->m[2], h->kdiag, h->omega, h->tau, *dpad);
+    SQ_CUDA(cudaGetLastError());
+
+    RecursionArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    for (int i = 0; i < 3; i++) {
+        a.n[i] = h->n[i];
+        a.m[i] = h->m[i];
+        a.nc[i] = h->nc[i];
+        a.pn[i] = h->pn[i];
+        a.fac_off[i] = h->fac2_off[i];
+        a.fac64_off[i] = h->fac64_off[i];
+        for (int j = 1; j <= h->p; j++) a.w[i][j - 1] = (T)(-h->fd[j] / (2.0 * h->h[i] * h->h[i] * h->tau));
+    }
+    a.nc3 = h->nc3;
+    a.N_d = h->N_d;
+    a.K = K;
+    a.natom = h->natom;
+    a.nproj = h->nproj;
+    a.want_force = want_force;
+    a.dpad = *dpad;
+    a.kappa[0] = (T)(h->cl[0] * h->dV * h->Nnorm * h->Nnorm / h->tau);
+    a.kappa[1] = (T)(h->cl[1] * h->dV * h->Nnorm * h->Nnorm / h->tau);
+    if constexpr (sizeof(T) == 8) a.fac = reinterpret_cast<const T *>(h->d_fac2_64);
+    else a.fac = reinterpret_cast<const T *>(h->d_fac2_32);
+    a.fac_stride = h->fac2_stride;
+    a.fac64 = h->d_fac64;
+    a.fac64_stride = h->fac64_stride;
+    a.sup_start = h->d_sup;
+    a.sup_len = h->d_sup + 3 * (h->natom > 0 ? h->natom : 1);
+    a.Nnorm = h->Nnorm;
+    a.mu = reinterpret_cast<T *>(h->d_mu);
+    a.A = want_force ? h->d_A : nullptr;
+
+    const int block = 256;
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+    const size_t smem_vec = recursion_smem_bytes<T>(h->natom, h->nc3, 1, block);
+    const size_t smem_glob = recursion_smem_bytes<T>(h->natom, h->nc3, 0, block);
+    // vectors in shared memory when that still allows two CTAs per SM, else in global scratch
+    a.vec_in_smem = (smem_vec * 2 + 2048 <= (size_t)dev_smem) ? 1 : 0;
+    const size_t smem = a.vec_in_smem ? smem_vec : smem_glob;
+    if (smem > (size_t)dev_smem) return fail(SQ_ERR_UNSUPPORTED, "too many atoms for shared memory (%zu B)", smem);
+    int per_sm = recursion_blocks_per_sm<T>(h->p, block, smem);
+    if (per_sm < 1) return fail(SQ_ERR_UNSUPPORTED, "recursion kernel does not fit on an SM");
+    long long grid = (long long)per_sm * h->num_sms;
+    if (grid > h->N_d) grid = h->N_d;
+    if (!a.vec_in_smem) {
+        if ((s = ensure(&h->d_scratch, &h->scratch_cap, sizeof(T) * 2 * (size_t)h->nc3 * grid))) return s;
+        a.scratch = reinterpret_cast<T *>(h->d_scratch);
+    }
+    SQ_CUDA(cudaEventRecord(h->ev[0], stream));
+    SQ_COUNT(1);
+    SQ_CUDA(launch_recursion<T>(a, h->p, (int)grid, block, smem, stream));
+    SQ_CUDA(cudaEventRecord(h->ev[1], stream));
+    // moment sums
+    dim3 g2(kSumBlocks, K + 1);
+    SQ_COUNT(1);
+    k_msum_partial<T><<<g2, 256, 0, stream>>>(reinterpret_cast<const T *>(h->d_mu), h->N_d, K, h->d_msum_part);
+    SQ_CUDA(cudaGetLastError());
+    return SQ_OK;
+}
+
+// Fermi level, weights and (optionally) the density from the stored moment sums.
+static sq_status fermi_and_density(sq_handle h, double kT, double N_e, double *d_rho, double *lambda_f,
+                                   cudaStream_t stream)
+{
+    const int K = h->K;
+    // M = 2^ceil(log2 max(4(K+1), 16 tau/kT))
+    const double need = fmax(4.0 * (K + 1), 16.0 * h->tau / kT);
+    int M = 1;
+    while (M < need) M <<= 1;
+    if (M > (1 << 26)) return fail(SQ_ERR_UNSUPPORTED, "kT/tau too small: %d Chebyshev nodes", M);
+    sq_status s;
+    if ((s = ensure(&h->d_nodes, &h->nodes_cap, sizeof(double) * 5 * (size_t)M))) return s;
+    if ((s = ensure(&h->d_coef, &h->coef_cap, sizeof(double) * 3 * (size_t)(K + 1)))) return s;
+    double *lam = h->d_nodes, *D = h->d_nodes + M, *f0 = h->d_nodes + 2 * M, *f1 = h->d_nodes + 3 * M,
+           *f2 = h->d_nodes + 4 * M;
+    SQ_CUDA(cudaEventRecord(h->ev[3], stream));
+    SQ_COUNT(1);
+    k_nodes<<<grid_for(M, 256, h->num_sms), 256, 0, stream>>>(h->d_msum, K, M, h->omega, h->tau, lam, D);
+    SQ_CUDA(cudaGetLastError());
+    // bisection state lives in the small scratch (after the first 256 bytes)
+    FermiState *st = reinterpret_cast<FermiState *>(reinterpret_cast<char *>(h->d_small) + 256);
+    double *part = reinterpret_cast<double *>(reinterpret_cast<char *>(h->d_small) + 512);
+    FermiState init;
+    memset(&init, 0, sizeof(init));
+    init.lo = h->lmin;
+    init.hi = h->lmax_;
+    SQ_CUDA(cudaMemcpyAsync(st, &init, sizeof(init), cudaMemcpyHostToDevice, stream));
+    FermiState fin;
+    for (int round = 0; round < 16; round++) {
+        SQ_COUNT(16);
+        for (int i = 0; i < 16; i++) k_fermi_step<<<kFermiBlocks, 256, 0, stream>>>(lam, D, M, kT, N_e, st, part);
+        SQ_CUDA(cudaGetLastError());
+        SQ_CUDA(cudaMemcpyAsync(&fin, st, sizeof(fin), cudaMemcpyDeviceToHost, stream));
+        SQ_CUDA(cudaStreamSynchronize(stream));
+        if (fin.phase >= 3) break;
+    }
+    if (fin.phase == 4)
+        return fail(SQ_ERR_NO_BRACKET, "N(lambda_min) = %.6g, N(lambda_max) = %.6g, N_e = %.6g", fin.N_lo, fin.N_hi, N_e);
+    if (fin.phase != 3) return fail(SQ_ERR_TIMEOUT, "bisection did not finish");
+    const double lf = fin.x;
+    if (!std::isfinite(lf)) return fail(SQ_ERR_NOT_FINITE, "Fermi level is not finite");
+    SQ_COUNT(2);
+    k_node_functions<<<grid_for(M, 256, h->num_sms), 256, 0, stream>>>(lam, M, lf, kT, f0, f1, f2);
+    SQ_CUDA(cudaGetLastError());
+    k_coeffs<<<dim3(K + 1, 3), 256, 0, stream>>>(f0, f1, f2, M, K, h->d_coef);
+    SQ_CUDA(cudaGetLastError());
+    if (d_rho) {
+        SQ_COUNT(1);
+        if (h->precision == SQ_FP64)
+            k_density<double><<<grid_for(h->N_d, 256, h->num_sms), 256, 0, stream>>>(
+                reinterpret_cast<const double *>(h->d_mu), h->N_d, K, h->d_coef, 1.0 / h->dV, d_rho);
+        else
+            k_density<float><<<grid_for(h->N_d, 256, h->num_sms), 256, 0, stream>>>(
+                reinterpret_cast<const float *>(h->d_mu), h->N_d, K, h->d_coef, 1.0 / h->dV, d_rho);
+        SQ_CUDA(cudaGetLastError());
+    }
+    SQ_CUDA(cudaEventRecord(h->ev[4], stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    h->kT = kT;
+    h->N_e = N_e;
+    h->lam_f = lf;
+    h->M = M;
+    if (lambda_f) *lambda_f = lf;
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_density(sq_handle h, int K, double kT, double N_e, int precision, int flags, double *d_rho,
+                                double *lambda_f, void *stream_)
+{
+    g_last_error[0] = 0;
+    if (!h || !d_rho || !lambda_f) return fail(SQ_ERR_ARG, "null argument");
+    if (K < 1 || K > 4096) return fail(SQ_ERR_ARG, "K = %d", K);
+    if (!(kT > 0) || !std::isfinite(kT)) return fail(SQ_ERR_ARG, "kT = %g", kT);
+    if (!(N_e > 0) || !(N_e < 2.0 * h->N_d)) return fail(SQ_ERR_ARG, "N_e = %g", N_e);
+    if (precision != SQ_FP64 && precision != SQ_FP32) return fail(SQ_ERR_ARG, "precision %d", precision);
+    if (flags & ~SQ_WANT_FORCE) return fail(SQ_ERR_ARG, "flags %d", flags);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int want_force = (flags & SQ_WANT_FORCE) && h->natom > 0;
+    h->have_density = 0;
+    sq_status s;
+    const size_t esz = precision == SQ_FP64 ? 8 : 4;
+    if ((s = ensure(&h->d_mu, &h->mu_bytes, esz * (size_t)(K + 1) * h->N_d))) return s;
+    if ((s = ensure(&h->d_msum, &h->msum_cap, sizeof(double) * (size_t)(K + 1)))) return s;
+    if ((s = ensure(&h->d_msum_part, &h->part_cap, sizeof(double) * (size_t)(K + 1) * kSumBlocks))) return s;
+    if (want_force) {
+        const size_t abytes = sizeof(double) * (size_t)(K + 1) * h->natom * h->nproj * 3;
+        if ((s = ensure(&h->d_A, &h->A_cap, abytes))) return s;
+        SQ_CUDA(cudaMemsetAsync(h->d_A, 0, abytes, stream));
+    }
+    h->precision = precision;
+    h->K = K;
+    s = precision == SQ_FP64 ? run_recursion<double>(h, K, want_force, stream)
+                             : run_recursion<float>(h, K, want_force, stream);
+    if (s) return s;
+    int *d_bad = reinterpret_cast<int *>(h->d_small);
+    SQ_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), stream));
+    SQ_COUNT(1);
+    k_msum_final<<<1, 256, 0, stream>>>(h->d_msum_part, kSumBlocks, K, h->d_msum, d_bad);
+    SQ_CUDA(cudaGetLastError());
+    SQ_CUDA(cudaEventRecord(h->ev[2], stream));
+    int bad = 0;
+    SQ_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    if (bad) return fail(SQ_ERR_NOT_FINITE, "moment sums are not finite");
+    if ((s = fermi_and_density(h, kT, N_e, d_rho, lambda_f, stream))) return s;
+    SQ_CUDA(cudaEventElapsedTime(&h->t_rec, h->ev[0], h->ev[1]));
+    SQ_CUDA(cudaEventElapsedTime(&h->t_msum, h->ev[1], h->ev[2]));
+    SQ_CUDA(cudaEventElapsedTime(&h->t_fermi, h->ev[3], h->ev[4]));
+    h->have_force = want_force;
+    h->have_density = 1;
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_fermi_level(sq_handle h, double kT, double N_e, double *d_rho, double *lambda_f,
+                                    void *stream_)
+{
+    g_last_error[0] = 0;
+    if (!h || !lambda_f) return fail(SQ_ERR_ARG, "null argument");
+    if (!h->have_density) return fail(SQ_ERR_STATE, "sq_fermi_level before sq_density");
+    if (!(kT > 0) || !(N_e > 0) || !(N_e < 2.0 * h->N_d)) return fail(SQ_ERR_ARG, "kT = %g, N_e = %g", kT, N_e);
+    return fermi_and_density(h, kT, N_e, d_rho, lambda_f, (cudaStream_t)stream_);
+}
+
+extern "C" sq_status sq_energy(sq_handle h, double *U, double *S, double *F, void *stream_)
+{
+    g_last_error[0] = 0;
+    if (!h) return fail(SQ_ERR_ARG, "null handle");
+    if (!h->have_density) return fail(SQ_ERR_STATE, "sq_energy before sq_density");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    double *d_out = reinterpret_cast<double *>(h->d_small) + 4;
+    SQ_COUNT(1);
+    k_energy<<<1, 32, 0, stream>>>(h->d_msum, h->d_coef, h->K, d_out);
+    SQ_CUDA(cudaGetLastError());
+    double out[2];
+    SQ_CUDA(cudaMemcpyAsync(out, d_out, sizeof(out), cudaMemcpyDeviceToHost, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    if (U) *U = out[0];
+    if (S) *S = out[1];
+    if (F) *F = out[0] - h->kT * out[1];
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_nonlocal_force(sq_handle h, double *d_force, void *stream_)
+{
+    g_last_error[0] = 0;
+    if (!h || (!d_force && h->natom > 0)) return fail(SQ_ERR_ARG, "null argument");
+    if (!h->have_density) return fail(SQ_ERR_STATE, "sq_nonlocal_force before sq_density");
+    if (h->natom == 0) return SQ_OK;
+    if (!h->have_force) return fail(SQ_ERR_STATE, "sq_density was called without SQ_WANT_FORCE");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    SQ_COUNT(1);
+    k_force<<<grid_for(3LL * h->natom, 128, h->num_sms), 128, 0, stream>>>(
+        h->d_A, h->d_coef, h->K, h->natom, h->nproj, h->cl[0], h->cl[1], h->dV, d_force);
+    SQ_CUDA(cudaGetLastError());
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_get_spectral_bounds(sq_handle h, double *lambda_min, double *lambda_max)
+{
+    if (!h) return fail(SQ_ERR_ARG, "null handle");
+    if (lambda_min) *lambda_min = h->lmin;
+    if (lambda_max) *lambda_max = h->lmax_;
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_get_moments(sq_handle h, int *K, int *precision, const void **d_mu, const double **d_msum)
+{
+    if (!h) return fail(SQ_ERR_ARG, "null handle");
+    if (!h->have_density) return fail(SQ_ERR_STATE, "no moments yet");
+    if (K) *K = h->K;
+    if (precision) *precision = h->precision;
+    if (d_mu) *d_mu = h->d_mu;
+    if (d_msum) *d_msum = h->d_msum;
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_copy_moments(sq_handle h, void *d_mu, double *d_msum, void *stream_)
+{
+    if (!h) return fail(SQ_ERR_ARG, "null handle");
+    if (!h->have_density) return fail(SQ_ERR_STATE, "no moments yet");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const size_t esz = h->precision == SQ_FP64 ? 8 : 4;
+    if (d_mu) SQ_CUDA(cudaMemcpyAsync(d_mu, h->d_mu, esz * (size_t)(h->K + 1) * h->N_d, cudaMemcpyDeviceToDevice, stream));
+    if (d_msum) SQ_CUDA(cudaMemcpyAsync(d_msum, h->d_msum, sizeof(double) * (h->K + 1), cudaMemcpyDeviceToDevice, stream));
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_get_timing(sq_handle h, double *recursion_ms, double *msum_ms, double *fermi_ms)
+{
+    if (!h) return fail(SQ_ERR_ARG, "null handle");
+    if (!h->have_density) return fail(SQ_ERR_STATE, "no sq_density yet");
+    if (recursion_ms) *recursion_ms = h->t_rec;
+    if (msum_ms) *msum_ms = h->t_msum;
+    if (fermi_ms) *fermi_ms = h->t_fermi;
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_get_cube(sq_handle h, int m[3])
+{
+    if (!h || !m) return fail(SQ_ERR_ARG, "null argument");
+    for (int a = 0; a < 3; a++) m[a] = h->m[a];
+    return SQ_OK;
+}

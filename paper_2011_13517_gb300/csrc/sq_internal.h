@@ -1,0 +1,64 @@
+// Internal declarations shared by the translation units of libsq (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sq.h"
+
+namespace sq {
+
+constexpr int kMaxHalfWidth = 8;   // FD order <= 16
+constexpr int kNumFactors = 4;     // g, hp (p factor), g', hp' per atom and axis
+
+// Per-precision device data derived from the handle for one recursion launch.
+template <typename T>
+struct RecursionArgs {
+    int n[3];            // grid points per axis
+    int m[3];            // cube half-widths
+    int nc[3];           // cube extents 2m+1
+    int nc3;             // cube points
+    long long N_d;       // grid points
+    int K;               // polynomial order
+    int natom;
+    int nproj;           // 1 (s) or 4 (s + p)
+    int want_force;
+    // scaled operator Hhat = (H - omega)/tau
+    const T *dpad;       // Hhat diagonal on the periodically padded grid [n3+2m3][n2+2m2][n1+2m1]
+    int pn[3];           // padded extents
+    T w[3][kMaxHalfWidth];   // Hhat off-diagonal weights w[a][j-1] = -c_j / (2 h_a^2 tau)
+    T kappa[2];          // c_l dV N^2 / tau for l = 0, 1
+    // projector factor tables, doubled along each axis: element (J, a, f, i), i in [0, 2 n_a),
+    // at J*fac_stride + fac_off[a] + f*2*n_a + i, equal to factor f of atom J on axis a at grid
+    // index i mod n_a
+    const T *fac;
+    int fac_off[3];
+    int fac_stride;
+    const double *fac64; // FP64 tables [natom][3][4][n_a] (values of chi at the column centre)
+    int fac64_off[3];
+    int fac64_stride;
+    const int *sup_start;   // [natom][3] first grid index of the support along each axis
+    const int *sup_len;     // [natom][3] support length (n_a = whole axis)
+    double Nnorm;        // projector normalisation N
+    // outputs
+    T *mu;               // [K+1][N_d]
+    double *A;           // [K+1][natom][nproj][3] (accumulated with atomics) or null
+    // vector storage
+    T *scratch;          // [gridDim][2][nc3] when the vectors live in global memory
+    int vec_in_smem;
+};
+
+// Launch the per-column recursion for all N_d columns.  Returns cudaSuccess or the launch error.
+template <typename T>
+cudaError_t launch_recursion(const RecursionArgs<T> &args, int fd_half, int grid, int block,
+                             size_t smem, cudaStream_t stream);
+
+// Dynamic shared memory needed for one CTA of the recursion kernel.
+template <typename T>
+size_t recursion_smem_bytes(int natom, int nc3, int vec_in_smem, int block);
+
+// Occupancy helper: active CTAs per SM for the given configuration.
+template <typename T>
+int recursion_blocks_per_sm(int fd_half, int block, size_t smem);
+
+}  // namespace sq

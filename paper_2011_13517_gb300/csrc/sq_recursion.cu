@@ -1,0 +1,450 @@
+// Per-grid-point Chebyshev recursion of the truncated Kohn-Sham Hamiltonian (the SQ hot loop).
+//
+// For every grid point q (a "column"), with the cube C_q of half-width m around q and the scaled
+// restricted operator Hhat_q = P_q (H - omega)/tau P_q (Sec. 3 "Hamiltonian at each grid point",
+// Sec. 2.2 scale and shift), the kernel runs the three-term recursion of Eq. Chebyshev,
+//     v_0 = e_q,  v_1 = Hhat_q v_0,  v_{k+1} = 2 Hhat_q v_k - v_{k-1},
+// and records mu_k^q = v_k(q).  With force moments requested it also accumulates
+//     A_k^{J,lm,d} += chi_Jlm(x_q) (d_d chi_Jlm)^T v_k        (Eq. NLforceSQ),
+// for the atoms whose projectors are nonzero at x_q.
+//
+// Mapping: one CTA owns one column at a time (persistent loop over columns).  Each recursion step
+// has two phases separated by CTA barriers:
+//   phase 1  warp-per-atom projector contractions chi^T v_k.  The projectors are separable, so each
+//            lane sums one x-row of the atom's support box against the 1D x factors and weights the
+//            row with the y and z factors; a warp shuffle reduction gives the 4 s/p dots (and the
+//            12 force dots for atoms that touch x_q).
+//   phase 2  thread-per-x-segment update: the segment and its x halo are held in registers, the y
+//            and z neighbours are read from the vector, the KB term is gathered from the atoms whose
+//            support covers the row, and w = a Hhat v_k - b v_{k-1} overwrites v_{k-1} in place.
+// The two cube vectors live in shared memory when they fit, else in a per-CTA global scratch slot.
+#include <cuda_runtime.h>
+
+#include "sq_internal.h"
+
+namespace sq {
+namespace {
+
+constexpr int kSeg = 8;   // x-segment length of phase 2
+
+struct AtomRec {
+    int J;          // atom index
+    int fidx;       // index into the force table, or -1
+    short lo[3];    // bounding local range [lo, hi] of the support inside the cube, per axis
+    short hi[3];
+    int base[3];    // fac offset of factor 0 of this atom's window start, per axis
+};
+
+__device__ __forceinline__ int pmod(int a, int n)
+{
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide ordered compaction of a flag: returns this thread's output slot (or -1) and the
+// total count through *total.  `scan` holds >= 33 ints of shared memory.
+__device__ int block_compact(bool flag, int *scan, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    unsigned bal = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) scan[warp] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int w = 0; w < nwarp; w++) {
+            int c = scan[w];
+            scan[w] = acc;
+            acc += c;
+        }
+        scan[32] = acc;
+    }
+    __syncthreads();
+    int slot = flag ? scan[warp] + __popc(bal & ((1u << lane) - 1u)) : -1;
+    *total = scan[32];
+    __syncthreads();
+    return slot;
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) recursion_kernel(const RecursionArgs<T> args)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int natom = args.natom;
+    // shared memory carve-up
+    AtomRec *act = reinterpret_cast<AtomRec *>(smem_raw);
+    T *sdot = reinterpret_cast<T *>(act + natom);                       // [natom][4]
+    double *chiq = reinterpret_cast<double *>(sdot + 4 * natom + 1);   // [natom][4]
+    chiq = reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(chiq) + 15) & ~uintptr_t(15));
+    int *scan = reinterpret_cast<int *>(chiq + 4 * natom);             // [40]
+    T *vec = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(scan + 40) + 15) & ~uintptr_t(15));
+
+    const int ncx = args.nc[0], ncy = args.nc[1], ncz = args.nc[2];
+    const int nc3 = args.nc3;
+    T *va, *vb;
+    if (args.vec_in_smem) {
+        va = vec;
+        vb = vec + nc3;
+    } else {
+        va = args.scratch + (size_t)blockIdx.x * 2 * nc3;
+        vb = va + nc3;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int nproj = args.nproj;
+    const int centre = args.m[0] + ncx * (args.m[1] + ncy * args.m[2]);
+    const long long N_d = args.N_d;
+    const int nsx = (ncx + kSeg - 1) / kSeg;
+    const int nseg = nsx * ncy * ncz;
+    const size_t plane_p = (size_t)args.pn[0] * args.pn[1];
+
+    for (long long q = blockIdx.x; q < N_d; q += gridDim.x) {
+        const int q1 = (int)(q % args.n[0]);
+        const int q2 = (int)((q / args.n[0]) % args.n[1]);
+        const int q3 = (int)(q / ((long long)args.n[0] * args.n[1]));
+        const int qa[3] = {q1, q2, q3};
+        int wstart[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) wstart[a] = pmod(qa[a] - args.m[a], args.n[a]);
+
+        // ---- column set-up: atoms whose projector support meets the cube (ordered) ----------
+        int nact = 0;
+        for (int base = 0; base < natom; base += blockDim.x) {
+            const int J = base + threadIdx.x;
+            bool on = J < natom;
+            short lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+            if (on) {
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const int na = args.n[a], nca = args.nc[a];
+                    const int st = args.sup_start[J * 3 + a], len = args.sup_len[J * 3 + a];
+                    if (len >= na) {
+                        lo[a] = 0;
+                        hi[a] = (short)(nca - 1);
+                        continue;
+                    }
+                    const bool first_in = pmod(wstart[a] - st, na) < len;     // cube start inside support
+                    const int d = pmod(st - wstart[a], na);                   // support start offset
+                    const bool starts_in = d < nca;
+                    if (!first_in && !starts_in) {
+                        on = false;
+                        break;
+                    }
+                    const bool last_in = pmod(wstart[a] + nca - 1 - st, na) < len;
+                    lo[a] = (short)(first_in ? 0 : d);
+                    if (last_in || (first_in && starts_in && d > 0)) {
+                        hi[a] = (short)(nca - 1);
+                    } else {
+                        hi[a] = (short)pmod(st + len - 1 - wstart[a], na);
+                    }
+                }
+            }
+            int total;
+            const int slot = block_compact(on, scan, &total);
+            if (slot >= 0) {
+                AtomRec r;
+                r.J = J;
+                r.fidx = -1;
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    r.lo[a] = lo[a];
+                    r.hi[a] = hi[a];
+                    r.base[a] = J * args.fac_stride + args.fac_off[a] + wstart[a];
+                }
+                act[nact + slot] = r;
+            }
+            nact += total;
+        }
+        __syncthreads();
+        // force atoms: projectors nonzero at x_q; chi_Jlm(x_q) in FP64
+        if (args.want_force) {
+            for (int t = threadIdx.x; t < nact; t += blockDim.x) {
+                AtomRec &r = act[t];
+                const double *f = args.fac64 + (size_t)r.J * args.fac64_stride;
+                const double gx = f[args.fac64_off[0] + 0 * args.n[0] + q1];
+                const double gy = f[args.fac64_off[1] + 0 * args.n[1] + q2];
+                const double gz = f[args.fac64_off[2] + 0 * args.n[2] + q3];
+                if (gx != 0.0 && gy != 0.0 && gz != 0.0) {
+                    r.fidx = t;
+                    const double hx = f[args.fac64_off[0] + 1 * args.n[0] + q1];
+                    const double hy = f[args.fac64_off[1] + 1 * args.n[1] + q2];
+                    const double hz = f[args.fac64_off[2] + 1 * args.n[2] + q3];
+                    chiq[4 * t + 0] = args.Nnorm * gx * gy * gz;
+                    chiq[4 * t + 1] = args.Nnorm * hx * gy * gz;
+                    chiq[4 * t + 2] = args.Nnorm * gx * hy * gz;
+                    chiq[4 * t + 3] = args.Nnorm * gx * gy * hz;
+                }
+            }
+        }
+        // v_0 = e_q, v_{-1} = 0
+        for (int i = threadIdx.x; i < nc3; i += blockDim.x) {
+            va[i] = (i == centre) ? T(1) : T(0);
+            vb[i] = T(0);
+        }
+        if (threadIdx.x == 0) args.mu[q] = T(1);
+        __syncthreads();
+
+        T *vcur = va, *vprev = vb;
+        const size_t dbase = (size_t)q3 * plane_p + (size_t)q2 * args.pn[0] + q1;
+        const int two_nx = 2 * args.n[0], two_ny = 2 * args.n[1], two_nz = 2 * args.n[2];
+
+        for (int k = 0; k <= args.K; k++) {
+            // ---- phase 1: projector contractions of v_k -----------------------------------
+            const bool need_dots = k < args.K;
+            if (need_dots || args.want_force) {
+                for (int t = warp; t < nact; t += nwarp) {
+                    const AtomRec r = act[t];
+                    const bool frc = args.want_force && r.fidx >= 0;
+                    if (!need_dots && !frc) continue;
+                    const T *fx = args.fac + r.base[0];
+                    const T *fy = args.fac + r.base[1];
+                    const T *fz = args.fac + r.base[2];
+                    const int nry = r.hi[1] - r.lo[1] + 1;
+                    const int nrows = nry * (r.hi[2] - r.lo[2] + 1);
+                    T s0 = 0, spx = 0, spy = 0, spz = 0;
+                    T f[12];
+#pragma unroll
+                    for (int i = 0; i < 12; i++) f[i] = 0;
+                    for (int row = lane; row < nrows; row += 32) {
+                        const int b = r.lo[1] + row % nry;
+                        const int c = r.lo[2] + row / nry;
+                        const T *vr = vcur + (c * ncy + b) * ncx;
+                        T Gs = 0, Hs = 0, Gd = 0, Hd = 0;
+                        for (int a = r.lo[0]; a <= r.hi[0]; a++) {
+                            const T val = vr[a];
+                            Gs += fx[a] * val;
+                            if (nproj > 1) Hs += fx[two_nx + a] * val;
+                            if (frc) {
+                                Gd += fx[2 * two_nx + a] * val;
+                                if (nproj > 1) Hd += fx[3 * two_nx + a] * val;
+                            }
+                        }
+                        const T gy = fy[b], gz = fz[c];
+                        const T gyz = gy * gz;
+                        s0 += Gs * gyz;
+                        T hy = 0, hz = 0;
+                        if (nproj > 1) {
+                            hy = fy[two_ny + b];
+                            hz = fz[two_nz + c];
+                            spx += Hs * gyz;
+                            spy += Gs * hy * gz;
+                            spz += Gs * gy * hz;
+                        }
+                        if (frc) {
+                            const T gdy = fy[2 * two_ny + b], gdz = fz[2 * two_nz + c];
+                            f[0] += Gd * gyz;          // s, d/dx
+                            f[1] += Gs * gdy * gz;     // s, d/dy
+                            f[2] += Gs * gy * gdz;     // s, d/dz
+                            if (nproj > 1) {
+                                const T hdy = fy[3 * two_ny + b], hdz = fz[3 * two_nz + c];
+                                f[3] += Hd * gyz;          // p_x
+                                f[4] += Hs * gdy * gz;
+                                f[5] += Hs * gy * gdz;
+                                f[6] += Gd * hy * gz;      // p_y
+                                f[7] += Gs * hdy * gz;
+                                f[8] += Gs * hy * gdz;
+                                f[9] += Gd * gy * hz;      // p_z
+                                f[10] += Gs * gdy * hz;
+                                f[11] += Gs * gy * hdz;
+                            }
+                        }
+                    }
+                    if (need_dots) {
+                        s0 = warp_sum(s0);
+                        if (nproj > 1) {
+                            spx = warp_sum(spx);
+                            spy = warp_sum(spy);
+                            spz = warp_sum(spz);
+                        }
+                        if (lane == 0) {
+                            sdot[4 * t + 0] = s0;
+                            sdot[4 * t + 1] = spx;
+                            sdot[4 * t + 2] = spy;
+                            sdot[4 * t + 3] = spz;
+                        }
+                    }
+                    if (frc) {
+                        const int nf = nproj > 1 ? 12 : 3;
+#pragma unroll
+                        for (int i = 0; i < 12; i++)
+                            if (i < nf) f[i] = warp_sum(f[i]);
+                        if (lane < nf) {
+                            T mine = f[0];
+#pragma unroll
+                            for (int i = 1; i < 12; i++)
+                                if (lane == i) mine = f[i];
+                            const int lm = lane / 3, d = lane % 3;
+                            const double val = chiq[4 * r.fidx + lm] * args.Nnorm * (double)mine;
+                            atomicAdd(args.A + ((((size_t)k * natom + r.J) * nproj + lm) * 3 + d), val);
+                        }
+                    }
+                }
+            }
+            if (k == args.K) break;
+            __syncthreads();
+
+            // ---- phase 2: w = ca Hhat v_k - cb v_{k-1}, written over v_{k-1} -------------------
+            const T ca = k == 0 ? T(1) : T(2);
+            const T cb = k == 0 ? T(0) : T(1);
+            for (int sg = threadIdx.x; sg < nseg; sg += blockDim.x) {
+                const int sx = sg % nsx;
+                const int rest = sg / nsx;
+                const int b = rest % ncy;
+                const int c = rest / ncy;
+                const int a0 = sx * kSeg;
+                const int rowbase = (c * ncy + b) * ncx;
+                T cen[kSeg + 2 * P];
+#pragma unroll
+                for (int i = 0; i < kSeg + 2 * P; i++) {
+                    const int a = a0 - P + i;
+                    cen[i] = (a >= 0 && a < ncx) ? vcur[rowbase + a] : T(0);
+                }
+                T acc[kSeg];
+                const T *drow = args.dpad + dbase + (size_t)c * plane_p + (size_t)b * args.pn[0];
+#pragma unroll
+                for (int s = 0; s < kSeg; s++) {
+                    const int a = a0 + s;
+                    T sum = 0;
+                    if (a < ncx) {
+                        sum = drow[a] * cen[P + s];
+#pragma unroll
+                        for (int j = 1; j <= P; j++) sum += args.w[0][j - 1] * (cen[P + s + j] + cen[P + s - j]);
+#pragma unroll
+                        for (int j = 1; j <= P; j++) {
+                            const T yp = (b + j < ncy) ? vcur[rowbase + a + j * ncx] : T(0);
+                            const T ym = (b - j >= 0) ? vcur[rowbase + a - j * ncx] : T(0);
+                            sum += args.w[1][j - 1] * (yp + ym);
+                        }
+#pragma unroll
+                        for (int j = 1; j <= P; j++) {
+                            const T zp = (c + j < ncz) ? vcur[rowbase + a + j * ncx * ncy] : T(0);
+                            const T zm = (c - j >= 0) ? vcur[rowbase + a - j * ncx * ncy] : T(0);
+                            sum += args.w[2][j - 1] * (zp + zm);
+                        }
+                    }
+                    acc[s] = sum;
+                }
+                // Kleinman-Bylander term, gathered from atoms whose support box covers this row
+                for (int t = 0; t < nact; t++) {
+                    const AtomRec &r = act[t];
+                    if (b < r.lo[1] || b > r.hi[1] || c < r.lo[2] || c > r.hi[2] ||
+                        a0 + kSeg - 1 < r.lo[0] || a0 > r.hi[0])
+                        continue;
+                    const T *fx = args.fac + r.base[0];
+                    const T gy = args.fac[r.base[1] + b], gz = args.fac[r.base[2] + c];
+                    const T s0 = sdot[4 * t];
+                    T alpha = args.kappa[0] * s0 * gy * gz;
+                    T beta = 0;
+                    if (nproj > 1) {
+                        const T hy = args.fac[r.base[1] + two_ny + b];
+                        const T hz = args.fac[r.base[2] + two_nz + c];
+                        alpha += args.kappa[1] * (sdot[4 * t + 2] * hy * gz + sdot[4 * t + 3] * gy * hz);
+                        beta = args.kappa[1] * sdot[4 * t + 1] * gy * gz;
+                    }
+#pragma unroll
+                    for (int s = 0; s < kSeg; s++) {
+                        const int a = a0 + s;
+                        if (a >= r.lo[0] && a <= r.hi[0]) {
+                            T add = fx[a] * alpha;
+                            if (nproj > 1) add += fx[two_nx + a] * beta;
+                            acc[s] += add;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int s = 0; s < kSeg; s++) {
+                    const int a = a0 + s;
+                    if (a < ncx) {
+                        const int idx = rowbase + a;
+                        vprev[idx] = ca * acc[s] - cb * vprev[idx];
+                    }
+                }
+            }
+            __syncthreads();
+            T *sw = vprev;
+            vprev = vcur;
+            vcur = sw;
+            if (threadIdx.x == 0) args.mu[(size_t)(k + 1) * N_d + q] = vcur[centre];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int P>
+cudaError_t launch_p(const RecursionArgs<T> &args, int grid, int block, size_t smem, cudaStream_t stream)
+{
+    auto kern = recursion_kernel<T, P>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, block, smem, stream>>>(args);
+    return cudaGetLastError();
+}
+
+template <typename T, int P>
+int blocks_p(int block, size_t smem)
+{
+    auto kern = recursion_kernel<T, P>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, block, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+}  // namespace
+
+template <typename T>
+size_t recursion_smem_bytes(int natom, int nc3, int vec_in_smem, int block)
+{
+    (void)block;
+    size_t s = sizeof(AtomRec) * (size_t)natom;
+    s += sizeof(T) * (4 * (size_t)natom + 1);
+    s = (s + 15) & ~size_t(15);
+    s += sizeof(double) * 4 * (size_t)natom;
+    s += sizeof(int) * 40;
+    s = (s + 15) & ~size_t(15);
+    if (vec_in_smem) s += sizeof(T) * 2 * (size_t)nc3;
+    return s + 32;
+}
+
+#define SQ_DISPATCH_P(FN, ...)                         \
+    switch (fd_half) {                                 \
+    case 1: return FN<T, 1>(__VA_ARGS__);              \
+    case 2: return FN<T, 2>(__VA_ARGS__);              \
+    case 3: return FN<T, 3>(__VA_ARGS__);              \
+    case 4: return FN<T, 4>(__VA_ARGS__);              \
+    case 5: return FN<T, 5>(__VA_ARGS__);              \
+    case 6: return FN<T, 6>(__VA_ARGS__);              \
+    case 7: return FN<T, 7>(__VA_ARGS__);              \
+    case 8: return FN<T, 8>(__VA_ARGS__);              \
+    default: break;                                    \
+    }
+
+template <typename T>
+cudaError_t launch_recursion(const RecursionArgs<T> &args, int fd_half, int grid, int block, size_t smem,
+                             cudaStream_t stream)
+{
+    SQ_DISPATCH_P(launch_p, args, grid, block, smem, stream)
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+int recursion_blocks_per_sm(int fd_half, int block, size_t smem)
+{
+    SQ_DISPATCH_P(blocks_p, block, smem)
+    return 0;
+}
+
+template cudaError_t launch_recursion<double>(const RecursionArgs<double> &, int, int, int, size_t, cudaStream_t);
+template cudaError_t launch_recursion<float>(const RecursionArgs<float> &, int, int, int, size_t, cudaStream_t);
+template size_t recursion_smem_bytes<double>(int, int, int, int);
+template size_t recursion_smem_bytes<float>(int, int, int, int);
+template int recursion_blocks_per_sm<double>(int, int, size_t);
+template int recursion_blocks_per_sm<float>(int, int, size_t);
+
+}  // namespace sq

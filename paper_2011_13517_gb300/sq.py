@@ -1,0 +1,234 @@
+"""Thin Python binding of libsq (include/sq.h): argument marshalling only.
+
+Every entry point has the name of the C function it calls.  Device buffers are torch CUDA tensors
+(passed as raw pointers with the current torch stream); host scalars come back as Python floats.
+If libsq.so is missing this module raises at import of the library -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsq.so")
+
+SQ_FP64 = 0
+SQ_FP32 = 1
+SQ_WANT_FORCE = 1
+
+STATUS = {0: "SQ_OK", 1: "SQ_ERR_ARG", 2: "SQ_ERR_CUBE_EXCEEDS_BOX", 3: "SQ_ERR_NO_BRACKET",
+          4: "SQ_ERR_NOT_FINITE", 5: "SQ_ERR_CUDA", 6: "SQ_ERR_TIMEOUT", 7: "SQ_ERR_OOM",
+          8: "SQ_ERR_STATE", 9: "SQ_ERR_UNSUPPORTED"}
+
+EXPORTS = ["sq_build_hamiltonian", "sq_density", "sq_fermi_level", "sq_energy", "sq_nonlocal_force",
+           "sq_get_spectral_bounds", "sq_get_moments", "sq_copy_moments", "sq_get_cube", "sq_get_timing",
+           "sq_kernel_launches", "sq_destroy", "sq_status_string", "sq_last_error"]
+
+
+class SQError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class sq_grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3), ("fd_order", ctypes.c_int)]
+
+
+class sq_atoms(ctypes.Structure):
+    _fields_ = [("natom", ctypes.c_int), ("R", ctypes.POINTER(ctypes.c_double)), ("lmax", ctypes.c_int),
+                ("sigma", ctypes.c_double), ("rc", ctypes.c_double),
+                ("energy", ctypes.POINTER(ctypes.c_double))]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsq.so (never builds implicitly; call paper_2011_13517_gb300.build.build() first)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsq.so not built ({LIB_PATH}); run paper_2011_13517_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+        L.sq_build_hamiltonian.argtypes = [ctypes.POINTER(sq_grid), vp, ctypes.POINTER(sq_atoms), ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, vp, ctypes.POINTER(vp)]
+        L.sq_density.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                 vp, dp, vp]
+        L.sq_fermi_level.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, dp, vp]
+        L.sq_energy.argtypes = [vp, dp, dp, dp, vp]
+        L.sq_nonlocal_force.argtypes = [vp, vp, vp]
+        L.sq_get_spectral_bounds.argtypes = [vp, dp, dp]
+        L.sq_get_moments.argtypes = [vp, ip, ip, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.sq_copy_moments.argtypes = [vp, vp, vp, vp]
+        L.sq_get_cube.argtypes = [vp, ip]
+        L.sq_get_timing.argtypes = [vp, dp, dp, dp]
+        L.sq_kernel_launches.argtypes = []
+        L.sq_destroy.argtypes = [vp]
+        L.sq_destroy.restype = None
+        L.sq_status_string.argtypes = [ctypes.c_int]
+        L.sq_status_string.restype = ctypes.c_char_p
+        L.sq_last_error.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("sq_destroy", "sq_status_string", "sq_last_error", "sq_kernel_launches"):
+                getattr(L, name).restype = ctypes.c_int
+        L.sq_kernel_launches.restype = ctypes.c_longlong
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise SQError(status, lib().sq_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype=torch.float64):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Handle:
+    """Owns an sq_handle and the host arrays its build call read."""
+
+    def __init__(self, ptr):
+        self.ptr = ctypes.c_void_p(ptr)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            lib().sq_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+
+def sq_build_hamiltonian(n, L, fd_order, d_veff, R, lmax, sigma, rc, energy, R_cut,
+                         lambda_min=math.nan, lambda_max=math.nan, stream=None) -> Handle:
+    """sq_build_hamiltonian: grid (n, L, fd_order), device V_eff [N_d] float64, atoms R [natom, 3]
+    with projector parameters, truncation half-width R_cut, optional spectral bounds."""
+    g = sq_grid()
+    for a in range(3):
+        g.n[a] = int(n[a])
+        g.L[a] = float(L[a])
+    g.fd_order = int(fd_order)
+    Rh = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(-1, 3))
+    en = np.ascontiguousarray(np.asarray(energy, dtype=np.float64).reshape(-1))
+    at = sq_atoms()
+    at.natom = int(Rh.shape[0])
+    at.R = Rh.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    at.lmax = int(lmax)
+    at.sigma = float(sigma)
+    at.rc = float(rc)
+    at.energy = en.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    out = ctypes.c_void_p()
+    _check(lib().sq_build_hamiltonian(ctypes.byref(g), _dev_ptr(d_veff), ctypes.byref(at), float(R_cut),
+                                      float(lambda_min), float(lambda_max), _stream(stream), ctypes.byref(out)))
+    return Handle(out.value)
+
+
+def sq_density(h: Handle, K, kT, N_e, precision, flags, d_rho, stream=None) -> float:
+    lam = ctypes.c_double()
+    _check(lib().sq_density(h.ptr, int(K), float(kT), float(N_e), int(precision), int(flags), _dev_ptr(d_rho),
+                            ctypes.byref(lam), _stream(stream)))
+    return lam.value
+
+
+def sq_fermi_level(h: Handle, kT, N_e, d_rho=None, stream=None) -> float:
+    lam = ctypes.c_double()
+    _check(lib().sq_fermi_level(h.ptr, float(kT), float(N_e),
+                                _dev_ptr(d_rho) if d_rho is not None else ctypes.c_void_p(None),
+                                ctypes.byref(lam), _stream(stream)))
+    return lam.value
+
+
+def sq_energy(h: Handle, stream=None):
+    U, S, F = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().sq_energy(h.ptr, ctypes.byref(U), ctypes.byref(S), ctypes.byref(F), _stream(stream)))
+    return U.value, S.value, F.value
+
+
+def sq_nonlocal_force(h: Handle, d_force, stream=None):
+    _check(lib().sq_nonlocal_force(h.ptr, _dev_ptr(d_force), _stream(stream)))
+
+
+def sq_get_spectral_bounds(h: Handle):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib().sq_get_spectral_bounds(h.ptr, ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def sq_get_cube(h: Handle):
+    m = (ctypes.c_int * 3)()
+    _check(lib().sq_get_cube(h.ptr, m))
+    return tuple(m)
+
+
+def sq_get_timing(h: Handle):
+    """(recursion_ms, moment_sum_ms, fermi_ms) of the last sq_density, from CUDA events."""
+    r, m, f = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().sq_get_timing(h.ptr, ctypes.byref(r), ctypes.byref(m), ctypes.byref(f)))
+    return r.value, m.value, f.value
+
+
+def sq_kernel_launches() -> int:
+    return int(lib().sq_kernel_launches())
+
+
+def sq_copy_moments(h: Handle, N_d, stream=None):
+    """Copies of the moments mu [K+1, N_d] (recursion precision) and sums M [K+1] (float64)."""
+    K, prec = ctypes.c_int(), ctypes.c_int()
+    mu_p, ms_p = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().sq_get_moments(h.ptr, ctypes.byref(K), ctypes.byref(prec), ctypes.byref(mu_p), ctypes.byref(ms_p)))
+    dt = torch.float64 if prec.value == SQ_FP64 else torch.float32
+    mu = torch.empty((K.value + 1, int(N_d)), dtype=dt, device="cuda")
+    ms = torch.empty(K.value + 1, dtype=torch.float64, device="cuda")
+    _check(lib().sq_copy_moments(h.ptr, ctypes.c_void_p(mu.data_ptr()), ctypes.c_void_p(ms.data_ptr()),
+                                 _stream(stream)))
+    return mu, ms
+
+
+# ---------------------------------------------------------------------------------------------
+# convenience for a generated cell (marshalling only)
+
+def build_for_cell(cell, bounds=None, stream=None, d_veff=None):
+    if d_veff is None:
+        d_veff = torch.from_numpy(np.ascontiguousarray(cell.veff.reshape(-1))).to("cuda")
+    lo, hi = (math.nan, math.nan) if bounds is None else bounds
+    return sq_build_hamiltonian(cell.n, cell.box, cell.fd_order, d_veff, cell.R, cell.lmax, cell.proj_sigma,
+                                cell.proj_rc, cell.proj_energy, cell.R_cut, lo, hi, stream=stream)
+
+
+def solve_cell(cell, precision=SQ_FP64, force=True, bounds=None, K=None, kT=None, N_e=None, stream=None):
+    """Build + density (+ energy, force) for one cell; returns numpy results."""
+    h = build_for_cell(cell, bounds=bounds, stream=stream)
+    try:
+        rho = torch.empty(cell.N_d, dtype=torch.float64, device="cuda")
+        lam_f = sq_density(h, cell.K if K is None else K, cell.kT if kT is None else kT,
+                           cell.N_e if N_e is None else N_e, precision, SQ_WANT_FORCE if force else 0, rho,
+                           stream=stream)
+        U, S, F = sq_energy(h, stream=stream)
+        out = dict(lam_f=lam_f, U=U, S=S, F=F, bounds=sq_get_spectral_bounds(h))
+        if force:
+            f = torch.empty((cell.natom, 3), dtype=torch.float64, device="cuda")
+            sq_nonlocal_force(h, f, stream=stream)
+            out["force"] = f.cpu().numpy()
+        mu, ms = sq_copy_moments(h, cell.N_d, stream=stream)
+        torch.cuda.synchronize()
+        out["rho"] = rho.cpu().numpy()
+        out["mu"] = mu.double().cpu().numpy()
+        out["Msum"] = ms.cpu().numpy()
+        return out
+    finally:
+        h.close()
