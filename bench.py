@@ -196,6 +196,8 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="both")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--profile", action="store_true",
+                    help="small case for ncu: one sq_density of the same cell with K=8, no timing loop")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -219,6 +221,8 @@ def main():
             dist.barrier()
 
     cell = cells.vacancy_cell()
+    if args.profile:
+        cell.K = 8
     stream = torch.cuda.current_stream()
     d_veff = torch.from_numpy(np.ascontiguousarray(cell.veff.reshape(-1))).cuda()
     rho = torch.empty(cell.N_d, dtype=torch.float64, device="cuda")
@@ -290,6 +294,12 @@ def main():
         bo = cell.N_d * 8 + cell.natom * 3 * 8
         return cell.N_d / statistics.mean(times), bi, bo
 
+    if args.profile:
+        for p in (["fp32", "fp64"] if args.precision == "both" else [args.precision]):
+            lam, U, S, timing = step(sq.SQ_FP32 if p == "fp32" else sq.SQ_FP64)
+            torch.cuda.synchronize()
+            print(json.dumps({"profile_case": p, "K": cell.K, "recursion_ms": timing[0], "lambda_f": lam}))
+        return
     flops = algorithmic_flops(cell)
     results = {}
     precs = ["fp32", "fp64"] if args.precision == "both" else [args.precision]
