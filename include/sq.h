@@ -191,6 +191,37 @@ sq_status sq_get_timing(sq_handle h, double *recursion_ms, double *msum_ms, doub
 /* Total number of kernels this library has launched in this process (for launch accounting). */
 long long sq_kernel_launches(void);
 
+/*
+ * sq_moments_noalloc -- the Chebyshev moments mu_k^q (k = 0..K, every grid point) of the handle's
+ * Hamiltonian, computed without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let the library allocate once their steady state has begun
+ * (a fixed device-memory budget handed out up front, a latency-critical loop where cudaMalloc and
+ * cudaFree would synchronise the device, or a GPU shared with other work whose footprint must not
+ * grow).  Set-up calls such as sq_build_hamiltonian still allocate; this call does not.
+ *
+ * It runs the same recursion kernel as sq_density (without force moments), but keeps the kernel's
+ * per-CTA cube vectors and the padded diagonal in one fixed 32 MiB device array that the library
+ * defines at file scope.  Every GPU that loads the library holds that array until the process
+ * exits, and all calls share it:
+ *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ *     caches it; make that first call before any stream capture;
+ *   - nothing in the array has to start at zero: each call rewrites every byte it reads, so it
+ *     does not depend on what an earlier call left there;
+ *   - calls whose kernels overlap on the GPU (other streams, other host threads) race on the array
+ *     and give wrong results; serialise them.
+ * Fewer CTAs run at once than in sq_density when a cube's two vectors are large, so it is slower.
+ *
+ *   h           handle from sq_build_hamiltonian, created on the current device
+ *   K           polynomial order, 1 <= K <= 4096
+ *   precision   SQ_FP64 or SQ_FP32
+ *   d_mu        device [K+1][N_d] output in the chosen precision (8 or 4 bytes per value),
+ *               caller-owned; the same values sq_density computes
+ * Errors: SQ_ERR_ARG; SQ_ERR_UNSUPPORTED when the padded diagonal plus one cube's two vectors do not
+ * fit in the 32 MiB array (or the device ordinal is >= 64); SQ_ERR_CUDA.  Asynchronous on `stream`;
+ * calls no allocating routine.
+ */
+sq_status sq_moments_noalloc(sq_handle h, int K, int precision, void *d_mu, void *stream);
+
 /* Release a handle and its device workspace (NULL is ignored).  Synchronises the device. */
 void sq_destroy(sq_handle h);
 

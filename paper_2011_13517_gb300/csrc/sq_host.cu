@@ -1016,3 +1016,122 @@ extern "C" sq_status sq_get_cube(sq_handle h, int m[3])
     for (int a = 0; a < 3; a++) m[a] = h->m[a];
     return SQ_OK;
 }
+
+// ------------------------------------------------------------------------------------------------
+// Allocation-free moments.
+//
+// Some callers cannot let the library allocate device memory once their steady state has begun:
+// applications that give the library a fixed device-memory budget up front, latency-critical loops
+// where cudaMalloc/cudaFree would synchronise the device, or code that must not grow the memory
+// footprint of a GPU it shares.  sq_moments_noalloc serves them: it runs the same per-column
+// recursion kernel as sq_density, but keeps that kernel's working vectors (and the padded Hhat
+// diagonal) in the fixed-size device array below instead of handle-owned allocations.
+//
+// The array is a file-scope __device__ object, so every GPU that loads this library holds it until
+// the process exits.  Host code cannot use the symbol itself as a device address; the address is
+// looked up with cudaGetSymbolAddress once per device (with that device current) and cached.
+
+static constexpr size_t kStaticScratchBytes = 32u << 20;   // 32 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+static constexpr int kMaxDevices = 64;
+static void *g_static_scratch_ptr[kMaxDevices] = {nullptr};
+
+static sq_status static_scratch_address(int dev, void **out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return fail(SQ_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    if (!g_static_scratch_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(SQ_ERR_CUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+        g_static_scratch_ptr[dev] = p;
+    }
+    *out = g_static_scratch_ptr[dev];
+    return SQ_OK;
+}
+
+template <typename T>
+static sq_status moments_noalloc(sq_handle h, int K, void *d_mu, cudaStream_t stream)
+{
+    void *base = nullptr;
+    sq_status s = static_scratch_address(h->dev, &base);
+    if (s) return s;
+    const size_t pad = (size_t)h->pn[0] * h->pn[1] * h->pn[2];
+    const size_t dpad_bytes = (sizeof(T) * pad + 255) & ~size_t(255);
+    const size_t per_cta = sizeof(T) * 2 * (size_t)h->nc3;
+    if (dpad_bytes + per_cta > kStaticScratchBytes)
+        return fail(SQ_ERR_UNSUPPORTED,
+                    "static scratch of %zu bytes cannot hold the padded diagonal (%zu B) and one cube's two "
+                    "vectors (%zu B)", kStaticScratchBytes, dpad_bytes, per_cta);
+    T *dpad = reinterpret_cast<T *>(base);
+    T *vecs = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(base) + dpad_bytes);
+    // every byte the kernels read is written first in this call: the diagonal here, and each
+    // column's vectors at the start of that column inside the recursion kernel
+    SQ_COUNT(1);
+    k_dpad<T><<<grid_for((long long)pad, 256, h->num_sms), 256, 0, stream>>>(
+        h->d_veff, h->n[0], h->n[1], h->n[2], h->m[0], h->m[1], h->m[2], h->kdiag, h->omega, h->tau, dpad);
+    SQ_CUDA(cudaGetLastError());
+
+    RecursionArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    for (int i = 0; i < 3; i++) {
+        a.n[i] = h->n[i];
+        a.m[i] = h->m[i];
+        a.nc[i] = h->nc[i];
+        a.pn[i] = h->pn[i];
+        a.fac_off[i] = h->fac2_off[i];
+        a.fac64_off[i] = h->fac64_off[i];
+        for (int j = 1; j <= h->p; j++) a.w[i][j - 1] = (T)(-h->fd[j] / (2.0 * h->h[i] * h->h[i] * h->tau));
+    }
+    a.nc3 = h->nc3;
+    a.N_d = h->N_d;
+    a.K = K;
+    a.natom = h->natom;
+    a.nproj = h->nproj;
+    a.want_force = 0;
+    a.dpad = dpad;
+    a.kappa[0] = (T)(h->cl[0] * h->dV * h->Nnorm * h->Nnorm / h->tau);
+    a.kappa[1] = (T)(h->cl[1] * h->dV * h->Nnorm * h->Nnorm / h->tau);
+    if constexpr (sizeof(T) == 8) a.fac = reinterpret_cast<const T *>(h->d_fac2_64);
+    else a.fac = reinterpret_cast<const T *>(h->d_fac2_32);
+    a.fac_stride = h->fac2_stride;
+    a.fac64 = h->d_fac64;
+    a.fac64_stride = h->fac64_stride;
+    a.sup_start = h->d_sup;
+    a.sup_len = h->d_sup + 3 * (h->natom > 0 ? h->natom : 1);
+    a.Nnorm = h->Nnorm;
+    a.mu = reinterpret_cast<T *>(d_mu);
+    a.A = nullptr;
+    a.vec_in_smem = 0;
+    a.scratch = vecs;
+
+    const int block = 256;
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+    const size_t smem = recursion_smem_bytes<T>(h->natom, h->nc3, 0, block);
+    if (smem > (size_t)dev_smem) return fail(SQ_ERR_UNSUPPORTED, "too many atoms for shared memory (%zu B)", smem);
+    const int per_sm = recursion_blocks_per_sm<T>(h->p, block, smem);
+    if (per_sm < 1) return fail(SQ_ERR_UNSUPPORTED, "recursion kernel does not fit on an SM");
+    long long grid = (long long)per_sm * h->num_sms;
+    const long long fit = (long long)((kStaticScratchBytes - dpad_bytes) / per_cta);
+    if (grid > fit) grid = fit;
+    if (grid > h->N_d) grid = h->N_d;
+    SQ_COUNT(1);
+    SQ_CUDA(launch_recursion<T>(a, h->p, (int)grid, block, smem, stream));
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_moments_noalloc(sq_handle h, int K, int precision, void *d_mu, void *stream_)
+{
+    g_last_error[0] = 0;
+    if (!h || !d_mu) return fail(SQ_ERR_ARG, "null argument");
+    if (K < 1 || K > 4096) return fail(SQ_ERR_ARG, "K = %d", K);
+    if (precision != SQ_FP64 && precision != SQ_FP32) return fail(SQ_ERR_ARG, "precision %d", precision);
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != h->dev)
+        return fail(SQ_ERR_ARG, "the handle's device (%d) is not the current device (%d)", h->dev, cur);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    return precision == SQ_FP64 ? moments_noalloc<double>(h, K, d_mu, stream)
+                                : moments_noalloc<float>(h, K, d_mu, stream);
+}

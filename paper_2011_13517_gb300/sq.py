@@ -26,7 +26,7 @@ STATUS = {0: "SQ_OK", 1: "SQ_ERR_ARG", 2: "SQ_ERR_CUBE_EXCEEDS_BOX", 3: "SQ_ERR_
 
 EXPORTS = ["sq_build_hamiltonian", "sq_density", "sq_fermi_level", "sq_energy", "sq_nonlocal_force",
            "sq_get_spectral_bounds", "sq_get_moments", "sq_copy_moments", "sq_get_cube", "sq_get_timing",
-           "sq_kernel_launches", "sq_destroy", "sq_status_string", "sq_last_error"]
+           "sq_kernel_launches", "sq_moments_noalloc", "sq_destroy", "sq_status_string", "sq_last_error"]
 
 
 class SQError(RuntimeError):
@@ -69,6 +69,7 @@ def lib():
         L.sq_get_cube.argtypes = [vp, ip]
         L.sq_get_timing.argtypes = [vp, dp, dp, dp]
         L.sq_kernel_launches.argtypes = []
+        L.sq_moments_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
         L.sq_destroy.argtypes = [vp]
         L.sq_destroy.restype = None
         L.sq_status_string.argtypes = [ctypes.c_int]
@@ -184,6 +185,14 @@ def sq_get_timing(h: Handle):
 
 def sq_kernel_launches() -> int:
     return int(lib().sq_kernel_launches())
+
+
+def sq_moments_noalloc(h: Handle, K, precision, d_mu, stream=None):
+    """sq_moments_noalloc: moments [K+1, N_d] into the caller's tensor (float64 for SQ_FP64, float32
+    for SQ_FP32) with no device allocation by the library; see include/sq.h for the shared fixed
+    scratch array and its rules."""
+    dt = torch.float64 if precision == SQ_FP64 else torch.float32
+    _check(lib().sq_moments_noalloc(h.ptr, int(K), int(precision), _dev_ptr(d_mu, dt), _stream(stream)))
 
 
 def sq_copy_moments(h: Handle, N_d, stream=None):
