@@ -79,13 +79,19 @@ class Cell:
         return 2 * self.m + 1
 
     def digest(self) -> str:
-        """Short hash of every input array, to detect generator drift between machines."""
-        hsh = hashlib.sha256()
-        for arr in (self.box, self.n, self.R, self.species, self.veff, self.proj_energy):
-            hsh.update(np.ascontiguousarray(arr).tobytes())
-        hsh.update(repr((self.fd_order, self.lmax, self.proj_sigma, self.proj_rc, self.R_cut,
-                         self.K, self.kT, self.N_e)).encode())
-        return hsh.hexdigest()[:16]
+        """Short hash of the inputs, to detect generator drift between machines.  Floating-point
+        arrays enter through sums, sums of squares and a few sampled values rounded to 10
+        significant digits, so last-ulp differences of the platform's libm do not change it."""
+        def sig(x):
+            return float(f"{float(x):.10g}")
+        v = self.veff.reshape(-1)
+        picks = np.linspace(0, v.size - 1, 16).astype(np.int64)
+        key = (tuple(int(x) for x in self.n), tuple(sig(x) for x in self.box), self.natom,
+               tuple(int(x) for x in self.species), sig(self.R.sum()), sig((self.R ** 2).sum()),
+               sig(v.sum()), sig((v * v).sum()), tuple(sig(v[i]) for i in picks),
+               tuple(sig(x) for x in self.proj_energy), self.fd_order, self.lmax, self.proj_sigma,
+               self.proj_rc, self.R_cut, self.K, self.kT, self.N_e)
+        return hashlib.sha256(repr(key).encode()).hexdigest()[:16]
 
 
 def _rng(seed: int, stream: int) -> np.random.Generator:

@@ -784,16 +784,23 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, cudaStream_t 
     a.mu = reinterpret_cast<T *>(h->d_mu);
     a.A = want_force ? h->d_A : nullptr;
 
-    const int block = 256;
     int dev_smem = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
-    const size_t smem_vec = recursion_smem_bytes<T>(h->natom, h->nc3, 1, block);
-    const size_t smem_glob = recursion_smem_bytes<T>(h->natom, h->nc3, 0, block);
-    // vectors in shared memory when that still allows two CTAs per SM, else in global scratch
-    a.vec_in_smem = (smem_vec * 2 + 2048 <= (size_t)dev_smem) ? 1 : 0;
+    const size_t smem_vec = recursion_smem_bytes<T>(h->natom, h->nc, 1);
+    const size_t smem_glob = recursion_smem_bytes<T>(h->natom, h->nc, 0);
+    // Vector placement: FP32 keeps both cube vectors in shared memory whenever they fit (512-thread
+    // CTAs for large cubes); FP64 only when two CTAs still fit per SM, else per-CTA global scratch.
+    const int nseg = ((h->nc[0] + 7) / 8) * h->nc[1] * h->nc[2];
+    int block = 256;
+    if (sizeof(T) == 4 && smem_vec <= (size_t)dev_smem) {
+        a.vec_in_smem = 1;
+        block = nseg >= 1024 ? 512 : 256;
+    } else {
+        a.vec_in_smem = (smem_vec * 2 + 2048 <= (size_t)dev_smem) ? 1 : 0;
+    }
     const size_t smem = a.vec_in_smem ? smem_vec : smem_glob;
     if (smem > (size_t)dev_smem) return fail(SQ_ERR_UNSUPPORTED, "too many atoms for shared memory (%zu B)", smem);
-    int per_sm = recursion_blocks_per_sm<T>(h->p, block, smem);
+    int per_sm = recursion_blocks_per_sm<T>(h->p, block, smem, a.vec_in_smem);
     if (per_sm < 1) return fail(SQ_ERR_UNSUPPORTED, "recursion kernel does not fit on an SM");
     long long grid = (long long)per_sm * h->num_sms;
     if (grid > h->N_d) grid = h->N_d;
@@ -1109,9 +1116,9 @@ static sq_status moments_noalloc(sq_handle h, int K, void *d_mu, cudaStream_t st
     const int block = 256;
     int dev_smem = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
-    const size_t smem = recursion_smem_bytes<T>(h->natom, h->nc3, 0, block);
+    const size_t smem = recursion_smem_bytes<T>(h->natom, h->nc, 0);
     if (smem > (size_t)dev_smem) return fail(SQ_ERR_UNSUPPORTED, "too many atoms for shared memory (%zu B)", smem);
-    const int per_sm = recursion_blocks_per_sm<T>(h->p, block, smem);
+    const int per_sm = recursion_blocks_per_sm<T>(h->p, block, smem, 0);
     if (per_sm < 1) return fail(SQ_ERR_UNSUPPORTED, "recursion kernel does not fit on an SM");
     long long grid = (long long)per_sm * h->num_sms;
     const long long fit = (long long)((kStaticScratchBytes - dpad_bytes) / per_cta);

@@ -55,10 +55,11 @@ cudaError_t launch_recursion(const RecursionArgs<T> &args, int fd_half, int grid
 
 // Dynamic shared memory needed for one CTA of the recursion kernel.
 template <typename T>
-size_t recursion_smem_bytes(int natom, int nc3, int vec_in_smem, int block);
+size_t recursion_smem_bytes(int natom, const int nc[3], int vec_in_smem);
 
-// Occupancy helper: active CTAs per SM for the given configuration.
+// Occupancy helper: active CTAs per SM for the given configuration (block 256 with vectors in global
+// scratch, or block 256/512 with vectors in shared memory).
 template <typename T>
-int recursion_blocks_per_sm(int fd_half, int block, size_t smem);
+int recursion_blocks_per_sm(int fd_half, int block, size_t smem, int vec_in_smem);
 
 }  // namespace sq

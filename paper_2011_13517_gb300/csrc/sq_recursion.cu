@@ -73,23 +73,30 @@ __device__ int block_compact(bool flag, int *scan, int *total)
     return slot;
 }
 
-template <typename T, int P>
-__global__ void __launch_bounds__(256) recursion_kernel(const RecursionArgs<T> args)
+template <typename T, int P, int BLOCK, bool VSMEM>
+__global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 2 : 1) recursion_kernel(const RecursionArgs<T> args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int natom = args.natom;
-    // shared memory carve-up
+    const int ncx = args.nc[0], ncy = args.nc[1], ncz = args.nc[2];
+    const int nc3 = args.nc3;
+    const int nsx = (ncx + kSeg - 1) / kSeg;
+    const int maskw = (natom + 31) / 32;     // mask words per row/plane/segment
+    // shared memory carve-up (sizes mirrored by recursion_smem_bytes)
     AtomRec *act = reinterpret_cast<AtomRec *>(smem_raw);
     T *sdot = reinterpret_cast<T *>(act + natom);                       // [natom][4]
     double *chiq = reinterpret_cast<double *>(sdot + 4 * natom + 1);   // [natom][4]
     chiq = reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(chiq) + 15) & ~uintptr_t(15));
     int *scan = reinterpret_cast<int *>(chiq + 4 * natom);             // [40]
-    T *vec = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(scan + 40) + 15) & ~uintptr_t(15));
+    // bit t of ymask[b] / zmask[c] / xmask[segment] is set when active atom t's support box covers
+    // y-row b / z-plane c / part of x-segment
+    unsigned *ymask = reinterpret_cast<unsigned *>(scan + 40);
+    unsigned *zmask = ymask + ncy * maskw;
+    unsigned *xmask = zmask + ncz * maskw;
+    T *vec = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(xmask + nsx * maskw) + 15) & ~uintptr_t(15));
 
-    const int ncx = args.nc[0], ncy = args.nc[1], ncz = args.nc[2];
-    const int nc3 = args.nc3;
     T *va, *vb;
-    if (args.vec_in_smem) {
+    if constexpr (VSMEM) {
         va = vec;
         vb = vec + nc3;
     } else {
@@ -100,7 +107,6 @@ __global__ void __launch_bounds__(256) recursion_kernel(const RecursionArgs<T> a
     const int nproj = args.nproj;
     const int centre = args.m[0] + ncx * (args.m[1] + ncy * args.m[2]);
     const long long N_d = args.N_d;
-    const int nsx = (ncx + kSeg - 1) / kSeg;
     const int nseg = nsx * ncy * ncz;
     const size_t plane_p = (size_t)args.pn[0] * args.pn[1];
 
@@ -115,7 +121,7 @@ __global__ void __launch_bounds__(256) recursion_kernel(const RecursionArgs<T> a
 
         // ---- column set-up: atoms whose projector support meets the cube (ordered) ----------
         int nact = 0;
-        for (int base = 0; base < natom; base += blockDim.x) {
+        for (int base = 0; base < natom; base += BLOCK) {
             const int J = base + threadIdx.x;
             bool on = J < natom;
             short lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -162,9 +168,34 @@ __global__ void __launch_bounds__(256) recursion_kernel(const RecursionArgs<T> a
             nact += total;
         }
         __syncthreads();
+        // coverage masks of the active atoms
+        {
+            const int wcol = (nact + 31) / 32;
+            const int nitems = (ncy + ncz + nsx) * maskw;
+            for (int it = threadIdx.x; it < nitems; it += BLOCK) {
+                const int w = it % maskw;
+                const int idx = it / maskw;
+                unsigned m = 0u;
+                if (w < wcol) {
+                    const int tend = min(nact, 32 * w + 32);
+                    for (int t = 32 * w; t < tend; t++) {
+                        const AtomRec &r = act[t];
+                        bool cov;
+                        if (idx < ncy) cov = idx >= r.lo[1] && idx <= r.hi[1];
+                        else if (idx < ncy + ncz) cov = (idx - ncy) >= r.lo[2] && (idx - ncy) <= r.hi[2];
+                        else {
+                            const int a0 = (idx - ncy - ncz) * kSeg;
+                            cov = r.lo[0] <= a0 + kSeg - 1 && r.hi[0] >= a0;
+                        }
+                        if (cov) m |= 1u << (t - 32 * w);
+                    }
+                }
+                ymask[it] = m;   // ymask, zmask and xmask are contiguous
+            }
+        }
         // force atoms: projectors nonzero at x_q; chi_Jlm(x_q) in FP64
         if (args.want_force) {
-            for (int t = threadIdx.x; t < nact; t += blockDim.x) {
+            for (int t = threadIdx.x; t < nact; t += BLOCK) {
                 AtomRec &r = act[t];
                 const double *f = args.fac64 + (size_t)r.J * args.fac64_stride;
                 const double gx = f[args.fac64_off[0] + 0 * args.n[0] + q1];
@@ -183,7 +214,7 @@ __global__ void __launch_bounds__(256) recursion_kernel(const RecursionArgs<T> a
             }
         }
         // v_0 = e_q, v_{-1} = 0
-        for (int i = threadIdx.x; i < nc3; i += blockDim.x) {
+        for (int i = threadIdx.x; i < nc3; i += BLOCK) {
             va[i] = (i == centre) ? T(1) : T(0);
             vb[i] = T(0);
         }
@@ -292,7 +323,7 @@ __global__ void __launch_bounds__(256) recursion_kernel(const RecursionArgs<T> a
             // ---- phase 2: w = ca Hhat v_k - cb v_{k-1}, written over v_{k-1} -------------------
             const T ca = k == 0 ? T(1) : T(2);
             const T cb = k == 0 ? T(0) : T(1);
-            for (int sg = threadIdx.x; sg < nseg; sg += blockDim.x) {
+            for (int sg = threadIdx.x; sg < nseg; sg += BLOCK) {
                 const int sx = sg % nsx;
                 const int rest = sg / nsx;
                 const int b = rest % ncy;
@@ -330,30 +361,33 @@ __global__ void __launch_bounds__(256) recursion_kernel(const RecursionArgs<T> a
                     }
                     acc[s] = sum;
                 }
-                // Kleinman-Bylander term, gathered from atoms whose support box covers this row
-                for (int t = 0; t < nact; t++) {
-                    const AtomRec &r = act[t];
-                    if (b < r.lo[1] || b > r.hi[1] || c < r.lo[2] || c > r.hi[2] ||
-                        a0 + kSeg - 1 < r.lo[0] || a0 > r.hi[0])
-                        continue;
-                    const T *fx = args.fac + r.base[0];
-                    const T gy = args.fac[r.base[1] + b], gz = args.fac[r.base[2] + c];
-                    const T s0 = sdot[4 * t];
-                    T alpha = args.kappa[0] * s0 * gy * gz;
-                    T beta = 0;
-                    if (nproj > 1) {
-                        const T hy = args.fac[r.base[1] + two_ny + b];
-                        const T hz = args.fac[r.base[2] + two_nz + c];
-                        alpha += args.kappa[1] * (sdot[4 * t + 2] * hy * gz + sdot[4 * t + 3] * gy * hz);
-                        beta = args.kappa[1] * sdot[4 * t + 1] * gy * gz;
-                    }
+                // Kleinman-Bylander term, gathered from the atoms whose support box covers this
+                // segment (intersection of the row, plane and segment coverage masks)
+                for (int w = 0; w < maskw; w++) {
+                    unsigned msk = ymask[b * maskw + w] & zmask[c * maskw + w] & xmask[sx * maskw + w];
+                    while (msk) {
+                        const int t = 32 * w + __ffs(msk) - 1;
+                        msk &= msk - 1u;
+                        const int bx = act[t].base[0], by = act[t].base[1], bz = act[t].base[2];
+                        const T *fx = args.fac + bx;
+                        const T gy = args.fac[by + b], gz = args.fac[bz + c];
+                        const T s0 = sdot[4 * t];
+                        T alpha = args.kappa[0] * s0 * gy * gz;
+                        T beta = 0;
+                        if (nproj > 1) {
+                            const T hy = args.fac[by + two_ny + b];
+                            const T hz = args.fac[bz + two_nz + c];
+                            alpha += args.kappa[1] * (sdot[4 * t + 2] * hy * gz + sdot[4 * t + 3] * gy * hz);
+                            beta = args.kappa[1] * sdot[4 * t + 1] * gy * gz;
+                        }
 #pragma unroll
-                    for (int s = 0; s < kSeg; s++) {
-                        const int a = a0 + s;
-                        if (a >= r.lo[0] && a <= r.hi[0]) {
-                            T add = fx[a] * alpha;
-                            if (nproj > 1) add += fx[two_nx + a] * beta;
-                            acc[s] += add;
+                        for (int s = 0; s < kSeg; s++) {
+                            const int a = a0 + s;
+                            if (a < ncx) {
+                                T add = fx[a] * alpha;
+                                if (nproj > 1) add += fx[two_nx + a] * beta;
+                                acc[s] += add;
+                            }
                         }
                     }
                 }
@@ -376,39 +410,58 @@ __global__ void __launch_bounds__(256) recursion_kernel(const RecursionArgs<T> a
     }
 }
 
-template <typename T, int P>
-cudaError_t launch_p(const RecursionArgs<T> &args, int grid, int block, size_t smem, cudaStream_t stream)
+template <typename T, int P, int BLOCK, bool VSMEM>
+cudaError_t launch_cfg(const RecursionArgs<T> &args, int grid, size_t smem, cudaStream_t stream)
 {
-    auto kern = recursion_kernel<T, P>;
+    auto kern = recursion_kernel<T, P, BLOCK, VSMEM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, block, smem, stream>>>(args);
+    kern<<<grid, BLOCK, smem, stream>>>(args);
     return cudaGetLastError();
 }
 
-template <typename T, int P>
-int blocks_p(int block, size_t smem)
+template <typename T, int P, int BLOCK, bool VSMEM>
+int blocks_cfg(size_t smem)
 {
-    auto kern = recursion_kernel<T, P>;
+    auto kern = recursion_kernel<T, P, BLOCK, VSMEM>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, block, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, BLOCK, smem) != cudaSuccess) return 0;
     return n;
+}
+
+// block 256 with vectors in global scratch, or block 512 with vectors in shared memory
+template <typename T, int P>
+cudaError_t launch_p(const RecursionArgs<T> &args, int grid, int block, size_t smem, cudaStream_t stream)
+{
+    if (args.vec_in_smem) return block == 512 ? launch_cfg<T, P, 512, true>(args, grid, smem, stream)
+                                             : launch_cfg<T, P, 256, true>(args, grid, smem, stream);
+    return launch_cfg<T, P, 256, false>(args, grid, smem, stream);
+}
+
+template <typename T, int P>
+int blocks_p(int block, size_t smem, int vec_in_smem)
+{
+    if (vec_in_smem) return block == 512 ? blocks_cfg<T, P, 512, true>(smem) : blocks_cfg<T, P, 256, true>(smem);
+    return blocks_cfg<T, P, 256, false>(smem);
 }
 
 }  // namespace
 
 template <typename T>
-size_t recursion_smem_bytes(int natom, int nc3, int vec_in_smem, int block)
+size_t recursion_smem_bytes(int natom, const int nc[3], int vec_in_smem)
 {
-    (void)block;
+    const size_t nc3 = (size_t)nc[0] * nc[1] * nc[2];
+    const int nsx = (nc[0] + kSeg - 1) / kSeg;
+    const int maskw = (natom + 31) / 32;
     size_t s = sizeof(AtomRec) * (size_t)natom;
     s += sizeof(T) * (4 * (size_t)natom + 1);
     s = (s + 15) & ~size_t(15);
     s += sizeof(double) * 4 * (size_t)natom;
     s += sizeof(int) * 40;
+    s += sizeof(unsigned) * (size_t)(nc[1] + nc[2] + nsx) * maskw;
     s = (s + 15) & ~size_t(15);
-    if (vec_in_smem) s += sizeof(T) * 2 * (size_t)nc3;
+    if (vec_in_smem) s += sizeof(T) * 2 * nc3;
     return s + 32;
 }
 
@@ -434,17 +487,17 @@ cudaError_t launch_recursion(const RecursionArgs<T> &args, int fd_half, int grid
 }
 
 template <typename T>
-int recursion_blocks_per_sm(int fd_half, int block, size_t smem)
+int recursion_blocks_per_sm(int fd_half, int block, size_t smem, int vec_in_smem)
 {
-    SQ_DISPATCH_P(blocks_p, block, smem)
+    SQ_DISPATCH_P(blocks_p, block, smem, vec_in_smem)
     return 0;
 }
 
 template cudaError_t launch_recursion<double>(const RecursionArgs<double> &, int, int, int, size_t, cudaStream_t);
 template cudaError_t launch_recursion<float>(const RecursionArgs<float> &, int, int, int, size_t, cudaStream_t);
-template size_t recursion_smem_bytes<double>(int, int, int, int);
-template size_t recursion_smem_bytes<float>(int, int, int, int);
-template int recursion_blocks_per_sm<double>(int, int, size_t);
-template int recursion_blocks_per_sm<float>(int, int, size_t);
+template size_t recursion_smem_bytes<double>(int, const int *, int);
+template size_t recursion_smem_bytes<float>(int, const int *, int);
+template int recursion_blocks_per_sm<double>(int, int, size_t, int);
+template int recursion_blocks_per_sm<float>(int, int, size_t, int);
 
 }  // namespace sq

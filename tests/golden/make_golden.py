@@ -25,8 +25,18 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("workload", choices=sorted(WORKLOADS))
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--refresh-digest", action="store_true",
+                    help="only recompute the input digest field of an existing file")
     args = ap.parse_args()
     cell = WORKLOADS[args.workload]()
+    if args.refresh_digest:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{cell.name}.json")
+        data = json.load(open(path))
+        data["digest"] = cell.digest()
+        with open(path, "w") as f:
+            json.dump(data, f, indent=1)
+        print(f"refreshed digest of {path}")
+        return
     t0 = time.time()
     r = oracle.sq_solve(cell, force=True, nthreads=args.threads)
     elapsed = time.time() - t0
