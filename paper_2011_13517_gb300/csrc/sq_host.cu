@@ -104,6 +104,7 @@ struct sq_handle_s {
     void *d_scratch = nullptr;      // per-CTA vectors when not in shared memory
     size_t scratch_cap = 0;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int kernel_used = 0;            // 0: generic recursion kernel, 1: FP32 slab kernel
     float t_rec = 0, t_msum = 0, t_fermi = 0;
 };
 
@@ -786,6 +787,37 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, cudaStream_t 
 
     int dev_smem = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+    if constexpr (sizeof(T) == 4) {
+        // FP32 on a cubic 21^3 / 25^3 cube with the 12th-order stencil: the slab kernel, sized by the
+        // largest number of atoms touching one cube
+        if (h->natom > 0 && slab_supported(h->nc, h->p)) {
+            int *d_cnt = reinterpret_cast<int *>(h->d_small) + 40;   // bytes 160..171 of the small scratch
+            SQ_CUDA(cudaMemsetAsync(d_cnt, 0, 3 * sizeof(int), stream));
+            SQ_COUNT(1);
+            SQ_CUDA(slab_counts(a, d_cnt, h->num_sms, stream));
+            int cnt[2];
+            SQ_CUDA(cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, stream));
+            SQ_CUDA(cudaStreamSynchronize(stream));
+            const int amax = cnt[0] > 0 ? cnt[0] : 1, fmax = cnt[1] > 0 ? cnt[1] : 1;
+            const size_t sm = slab_smem_bytes(h->nc[0], amax, fmax);
+            if (sm <= (size_t)dev_smem) {
+                long long grid = h->num_sms;
+                if (grid > h->N_d) grid = h->N_d;
+                h->kernel_used = 1;
+                SQ_CUDA(cudaEventRecord(h->ev[0], stream));
+                SQ_COUNT(1);
+                SQ_CUDA(launch_slab(a, amax, fmax, (int)grid, sm, d_cnt + 2, stream));
+                SQ_CUDA(cudaEventRecord(h->ev[1], stream));
+                dim3 g2(kSumBlocks, K + 1);
+                SQ_COUNT(1);
+                k_msum_partial<T><<<g2, 256, 0, stream>>>(reinterpret_cast<const T *>(h->d_mu), h->N_d, K,
+                                                          h->d_msum_part);
+                SQ_CUDA(cudaGetLastError());
+                return SQ_OK;
+            }
+        }
+    }
+    h->kernel_used = 0;
     const size_t smem_vec = recursion_smem_bytes<T>(h->natom, h->nc, 1);
     const size_t smem_glob = recursion_smem_bytes<T>(h->natom, h->nc, 0);
     // Vector placement: FP32 keeps both cube vectors in shared memory whenever they fit (512-thread
@@ -920,9 +952,13 @@ extern "C" sq_status sq_density(sq_handle h, int K, double kT, double N_e, int p
     k_msum_final<<<1, 256, 0, stream>>>(h->d_msum_part, kSumBlocks, K, h->d_msum, d_bad);
     SQ_CUDA(cudaGetLastError());
     SQ_CUDA(cudaEventRecord(h->ev[2], stream));
-    int bad = 0;
+    int bad = 0, slab_err = 0;
     SQ_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    if (h->kernel_used == 1)
+        SQ_CUDA(cudaMemcpyAsync(&slab_err, reinterpret_cast<int *>(h->d_small) + 42, sizeof(int),
+                                cudaMemcpyDeviceToHost, stream));
     SQ_CUDA(cudaStreamSynchronize(stream));
+    if (slab_err) return fail(SQ_ERR_UNSUPPORTED, "a column exceeded the slab kernel's atom capacity (%d)", slab_err);
     if (bad) return fail(SQ_ERR_NOT_FINITE, "moment sums are not finite");
     if ((s = fermi_and_density(h, kT, N_e, d_rho, lambda_f, stream))) return s;
     SQ_CUDA(cudaEventElapsedTime(&h->t_rec, h->ev[0], h->ev[1]));

@@ -62,4 +62,14 @@ size_t recursion_smem_bytes(int natom, const int nc[3], int vec_in_smem);
 template <typename T>
 int recursion_blocks_per_sm(int fd_half, int block, size_t smem, int vec_in_smem);
 
+// FP32 slab kernel (cubic cubes of 21 or 25 points, 12th-order FD): support test, shared memory
+// for a given active/force atom capacity, the per-column capacity pre-pass (counts[0] = max active
+// atoms, counts[1] = max force atoms; both must be zero-initialised) and the launch.  *err is set
+// nonzero if a column exceeded the capacities.
+bool slab_supported(const int nc[3], int fd_half);
+size_t slab_smem_bytes(int nc, int amax, int fmax);
+cudaError_t slab_counts(const RecursionArgs<float> &args, int *d_counts, int num_sms, cudaStream_t stream);
+cudaError_t launch_slab(const RecursionArgs<float> &args, int amax, int fmax, int grid, size_t smem, int *err,
+                        cudaStream_t stream);
+
 }  // namespace sq

@@ -1,0 +1,493 @@
+// FP32 per-column Chebyshev recursion for cubic truncation cubes of 17..32 points per axis: the
+// "slab" kernel.
+//
+// Same mathematics as recursion_kernel (Eq. Chebyshev on the truncated scaled Hamiltonian, with the
+// Kleinman-Bylander term and the force moments of Eq. NLforceSQ), mapped for the FP32 pipes:
+//   - one CTA per column, NC warps: warp b owns the y-slab b of the cube, lane a its x position;
+//     each lane keeps its z-pencil v(a, b, 0..NC-1) in registers for the whole step;
+//   - stencil: z neighbours from the lane's own registers, x neighbours by warp shuffles, y
+//     neighbours from the shared-memory copy of v_k (one conflict-free wavefront per load);
+//   - KB term: for every atom whose support covers slab b, the y factor is folded into two
+//     per-lane scalars, and the z factors come from shared-memory tables read as broadcasts;
+//   - projector contractions chi^T v: per-lane z sums, a warp reduction over x, per-warp slots in
+//     shared memory, then a fixed-order sum over the slabs (deterministic).
+#include <cuda_runtime.h>
+
+#include "sq_internal.h"
+
+namespace sq {
+namespace {
+
+struct SlabRec {
+    int J;          // atom index
+    int fidx;       // force slot or -1
+    short lo[3];    // bounding local range of the support inside the cube, per axis
+    short hi[3];
+};
+
+__device__ __forceinline__ int smod(int a, int n)
+{
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ float wsum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Support range of atom J's projector inside the cube window [wstart, wstart + nc) on one axis,
+// as a bounding local interval; false when they do not meet.  (Same rule as recursion_kernel.)
+__device__ __forceinline__ bool window_range(int st, int len, int na, int nca, int wstart, short &lo, short &hi)
+{
+    if (len >= na) {
+        lo = 0;
+        hi = (short)(nca - 1);
+        return true;
+    }
+    const bool first_in = smod(wstart - st, na) < len;
+    const int d = smod(st - wstart, na);
+    const bool starts_in = d < nca;
+    if (!first_in && !starts_in) return false;
+    const bool last_in = smod(wstart + nca - 1 - st, na) < len;
+    lo = (short)(first_in ? 0 : d);
+    hi = (last_in || (first_in && starts_in && d > 0)) ? (short)(nca - 1) : (short)smod(st + len - 1 - wstart, na);
+    return true;
+}
+
+struct SlabSmem {
+    float *va, *vb;
+    float2 *tab;     // [amax][3][NC] (g, hp) window tables
+    float2 *ftab;    // [fmax][3][NC] (g', hp') window tables of force atoms
+    float *slot;     // [NC][amax][4]
+    float *fslot;    // [NC][fmax][12]
+    float *sd;       // [amax][4]
+    SlabRec *rec;    // [amax]
+    double *chiq;    // [fmax][4]
+    int *ftl;        // [fmax] force slot -> active index
+    unsigned *ymask; // [NC][W]
+    int *scan;       // [40]
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <int NC>
+__host__ __device__ inline size_t slab_layout(unsigned char *base, int amax, int fmax, SlabSmem *s)
+{
+    const int W = (amax + 31) / 32;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align16(off + bytes);
+        return base ? base + o : nullptr;
+    };
+    const size_t nc3 = (size_t)NC * NC * NC;
+    unsigned char *p;
+    p = take(sizeof(float) * nc3);                        if (s) s->va = (float *)p;
+    p = take(sizeof(float) * nc3);                        if (s) s->vb = (float *)p;
+    p = take(sizeof(float2) * (size_t)amax * 3 * NC);     if (s) s->tab = (float2 *)p;
+    p = take(sizeof(float2) * (size_t)fmax * 3 * NC);     if (s) s->ftab = (float2 *)p;
+    p = take(sizeof(float) * (size_t)NC * amax * 4);      if (s) s->slot = (float *)p;
+    p = take(sizeof(float) * (size_t)NC * fmax * 12);     if (s) s->fslot = (float *)p;
+    p = take(sizeof(float) * (size_t)amax * 4);           if (s) s->sd = (float *)p;
+    p = take(sizeof(SlabRec) * (size_t)amax);             if (s) s->rec = (SlabRec *)p;
+    p = take(sizeof(double) * (size_t)fmax * 4);          if (s) s->chiq = (double *)p;
+    p = take(sizeof(int) * (size_t)fmax);                 if (s) s->ftl = (int *)p;
+    p = take(sizeof(unsigned) * (size_t)NC * W);          if (s) s->ymask = (unsigned *)p;
+    p = take(sizeof(int) * 40);                           if (s) s->scan = (int *)p;
+    return off;
+}
+
+// Ordered block-wide compaction (see recursion_kernel).
+__device__ int compact(bool flag, int *scan, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) scan[warp] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int w = 0; w < nwarp; w++) {
+            const int c = scan[w];
+            scan[w] = acc;
+            acc += c;
+        }
+        scan[32] = acc;
+    }
+    __syncthreads();
+    const int slot = flag ? scan[warp] + __popc(bal & ((1u << lane) - 1u)) : -1;
+    *total = scan[32];
+    __syncthreads();
+    return slot;
+}
+
+// Per-column counts of active atoms (support meets the cube) and force atoms (support holds x_q).
+__global__ void k_slab_counts(const RecursionArgs<float> args, int *counts)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < args.N_d;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int qa[3] = {(int)(q % args.n[0]), (int)((q / args.n[0]) % args.n[1]),
+                           (int)(q / ((long long)args.n[0] * args.n[1]))};
+        int nact = 0, nfrc = 0;
+        for (int J = 0; J < args.natom; J++) {
+            bool on = true, frc = true;
+            for (int ax = 0; ax < 3 && on; ax++) {
+                const int st = args.sup_start[J * 3 + ax], len = args.sup_len[J * 3 + ax];
+                short lo, hi;
+                on = window_range(st, len, args.n[ax], args.nc[ax], smod(qa[ax] - args.m[ax], args.n[ax]), lo, hi);
+                frc = frc && (len >= args.n[ax] || smod(qa[ax] - st, args.n[ax]) < len);
+            }
+            nact += on;
+            nfrc += on && frc;
+        }
+        atomicMax(counts, nact);
+        atomicMax(counts + 1, nfrc);
+    }
+}
+
+template <int NC, int P>
+__global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<float> args, int amax, int fmax,
+                                                          int *err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SlabSmem S;
+    slab_layout<NC>(smem_raw, amax, fmax, &S);
+    const int W = (amax + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const int b = threadIdx.x >> 5;          // slab (y index)
+    const bool live = lane < NC;             // lane holds a cube point
+    const int m = (NC - 1) / 2;
+    const int natom = args.natom;
+    const int nproj = args.nproj;
+    const long long N_d = args.N_d;
+    const size_t plane_p = (size_t)args.pn[0] * args.pn[1];
+    const float kap0 = args.kappa[0], kap1 = args.kappa[1];
+    const int two_n[3] = {2 * args.n[0], 2 * args.n[1], 2 * args.n[2]};
+
+    for (long long q = blockIdx.x; q < N_d; q += gridDim.x) {
+        const int qa[3] = {(int)(q % args.n[0]), (int)((q / args.n[0]) % args.n[1]),
+                           (int)(q / ((long long)args.n[0] * args.n[1]))};
+        int wstart[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) wstart[ax] = smod(qa[ax] - args.m[ax], args.n[ax]);
+
+        // ---- active atoms (ordered) ----
+        int nact = 0;
+        for (int base = 0; base < natom; base += NC * 32) {
+            const int J = base + (int)threadIdx.x;
+            bool on = J < natom;
+            short lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+            for (int ax = 0; ax < 3 && on; ax++)
+                on = window_range(args.sup_start[J * 3 + ax], args.sup_len[J * 3 + ax], args.n[ax], NC, wstart[ax],
+                                  lo[ax], hi[ax]);
+            int total;
+            const int slot = compact(on, S.scan, &total);
+            if (slot >= 0 && nact + slot < amax) {
+                SlabRec r;
+                r.J = J;
+                r.fidx = -1;
+                for (int ax = 0; ax < 3; ax++) {
+                    r.lo[ax] = lo[ax];
+                    r.hi[ax] = hi[ax];
+                }
+                S.rec[nact + slot] = r;
+            }
+            nact += total;
+        }
+        if (nact > amax) {   // cannot happen with the pre-pass capacity; report and skip the column
+            if (threadIdx.x == 0) atomicExch(err, 1);
+            continue;
+        }
+        __syncthreads();
+        // ---- window tables ----
+        for (int it = threadIdx.x; it < nact * 3 * NC; it += NC * 32) {
+            const int o = it % NC, ax = (it / NC) % 3, t = it / (3 * NC);
+            const float *f = args.fac + (size_t)S.rec[t].J * args.fac_stride + args.fac_off[ax] + wstart[ax] + o;
+            S.tab[it] = make_float2(f[0], f[two_n[ax]]);
+        }
+        // ---- force atoms: projectors nonzero at x_q ----
+        int nfrc = 0;
+        if (args.want_force) {
+            for (int base = 0; base < nact; base += NC * 32) {
+                const int t = base + (int)threadIdx.x;
+                bool on = false;
+                const double *f = nullptr;
+                if (t < nact) {
+                    f = args.fac64 + (size_t)S.rec[t].J * args.fac64_stride;
+                    on = f[args.fac64_off[0] + qa[0]] != 0.0 && f[args.fac64_off[1] + qa[1]] != 0.0 &&
+                         f[args.fac64_off[2] + qa[2]] != 0.0;
+                }
+                int total;
+                const int slot = compact(on, S.scan, &total);
+                if (slot >= 0 && nfrc + slot < fmax) {
+                    const int fi = nfrc + slot;
+                    S.rec[t].fidx = fi;
+                    S.ftl[fi] = t;
+                    const double gx = f[args.fac64_off[0] + qa[0]], hx = f[args.fac64_off[0] + args.n[0] + qa[0]];
+                    const double gy = f[args.fac64_off[1] + qa[1]], hy = f[args.fac64_off[1] + args.n[1] + qa[1]];
+                    const double gz = f[args.fac64_off[2] + qa[2]], hz = f[args.fac64_off[2] + args.n[2] + qa[2]];
+                    S.chiq[4 * fi + 0] = args.Nnorm * gx * gy * gz;
+                    S.chiq[4 * fi + 1] = args.Nnorm * hx * gy * gz;
+                    S.chiq[4 * fi + 2] = args.Nnorm * gx * hy * gz;
+                    S.chiq[4 * fi + 3] = args.Nnorm * gx * gy * hz;
+                }
+                nfrc += total;
+            }
+            if (nfrc > fmax) {
+                if (threadIdx.x == 0) atomicExch(err, 2);
+                continue;
+            }
+            __syncthreads();
+            for (int it = threadIdx.x; it < nfrc * 3 * NC; it += NC * 32) {
+                const int o = it % NC, ax = (it / NC) % 3, fi = it / (3 * NC);
+                const float *f = args.fac + (size_t)S.rec[S.ftl[fi]].J * args.fac_stride + args.fac_off[ax] +
+                                 wstart[ax] + o;
+                S.ftab[it] = make_float2(f[2 * two_n[ax]], f[3 * two_n[ax]]);
+            }
+        }
+        // ---- slab coverage masks ----
+        for (int it = threadIdx.x; it < NC * W; it += NC * 32) {
+            const int wd = it % W, bb = it / W;
+            unsigned msk = 0u;
+            for (int t = 32 * wd; t < min(nact, 32 * wd + 32); t++)
+                if (bb >= S.rec[t].lo[1] && bb <= S.rec[t].hi[1]) msk |= 1u << (t - 32 * wd);
+            S.ymask[it] = msk;
+        }
+        // ---- v_0 = e_q, v_{-1} = 0 ----
+        float vz[NC];
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+            vz[c] = (live && lane == m && b == m && c == m) ? 1.0f : 0.0f;
+            if (live) {
+                S.va[(c * NC + b) * NC + lane] = vz[c];
+                S.vb[(c * NC + b) * NC + lane] = 0.0f;
+            }
+        }
+        if (threadIdx.x == 0) args.mu[q] = 1.0f;
+        __syncthreads();
+        float *vcur = S.va, *vprev = S.vb;
+        const float *drow = args.dpad + (size_t)qa[2] * plane_p + (size_t)(qa[1] + b) * args.pn[0] + qa[0] + lane;
+
+        for (int k = 0; k <= args.K; k++) {
+            // ---- projector contractions of v_k (registers) -> per-slab slots ----
+            const bool need_dots = k < args.K;
+            if (need_dots || args.want_force) {
+                for (int wd = 0; wd < W; wd++) {
+                    unsigned msk = S.ymask[b * W + wd];
+                    while (msk) {
+                        const int t = 32 * wd + __ffs(msk) - 1;
+                        msk &= msk - 1u;
+                        const SlabRec r = S.rec[t];
+                        const bool frc = args.want_force && r.fidx >= 0;
+                        if (!need_dots && !frc) continue;
+                        const float2 *tz = S.tab + (t * 3 + 2) * NC;
+                        const float2 *fz = frc ? S.ftab + (r.fidx * 3 + 2) * NC : tz;
+                        float G = 0.f, H = 0.f, Gd = 0.f, Hd = 0.f;
+#pragma unroll
+                        for (int c0 = 0; c0 < NC; c0 += 4) {
+                            if (c0 + 3 < r.lo[2] || c0 > r.hi[2]) continue;
+#pragma unroll
+                            for (int cc = 0; cc < 4; cc++) {
+                                const int c = c0 + cc;
+                                if (c < NC) {
+                                    const float2 z = tz[c];
+                                    G += z.x * vz[c];
+                                    H += z.y * vz[c];
+                                    if (frc) {
+                                        const float2 zd = fz[c];
+                                        Gd += zd.x * vz[c];
+                                        Hd += zd.y * vz[c];
+                                    }
+                                }
+                            }
+                        }
+                        const float2 xv = live ? S.tab[(t * 3 + 0) * NC + lane] : make_float2(0.f, 0.f);
+                        const float u1 = wsum(xv.x * G), u2 = wsum(xv.y * G), u3 = wsum(xv.x * H);
+                        const float2 yv = S.tab[(t * 3 + 1) * NC + b];
+                        if (lane == 0) {
+                            float *sl = S.slot + ((size_t)b * amax + t) * 4;
+                            sl[0] = yv.x * u1;
+                            sl[1] = yv.x * u2;
+                            sl[2] = yv.y * u1;
+                            sl[3] = yv.x * u3;
+                        }
+                        if (frc) {
+                            const float2 xd = live ? S.ftab[(r.fidx * 3 + 0) * NC + lane] : make_float2(0.f, 0.f);
+                            const float v1 = wsum(xd.x * G), v3 = wsum(xv.x * Gd), v4 = wsum(xd.y * G);
+                            const float v6 = wsum(xv.y * Gd), v7 = wsum(xd.x * H), v9 = wsum(xv.x * Hd);
+                            const float2 yd = S.ftab[(r.fidx * 3 + 1) * NC + b];
+                            if (lane == 0) {
+                                float *fs = S.fslot + ((size_t)b * fmax + r.fidx) * 12;
+                                fs[0] = yv.x * v1;   // s,  d/dx
+                                fs[1] = yd.x * u1;   // s,  d/dy
+                                fs[2] = yv.x * v3;   // s,  d/dz
+                                fs[3] = yv.x * v4;   // px, d/dx
+                                fs[4] = yd.x * u2;   // px, d/dy
+                                fs[5] = yv.x * v6;   // px, d/dz
+                                fs[6] = yv.y * v1;   // py, d/dx
+                                fs[7] = yd.y * u1;   // py, d/dy
+                                fs[8] = yv.y * v3;   // py, d/dz
+                                fs[9] = yv.x * v7;   // pz, d/dx
+                                fs[10] = yd.x * u3;  // pz, d/dy
+                                fs[11] = yv.x * v9;  // pz, d/dz
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // fixed-order sum of the slab slots: dots of v_k, and force moments A_k
+            if (need_dots) {
+                for (int it = threadIdx.x; it < nact * 4; it += NC * 32) {
+                    const int t = it >> 2, comp = it & 3;
+                    float s = 0.f;
+                    for (int bb = 0; bb < NC; bb++)
+                        if ((S.ymask[bb * W + (t >> 5)] >> (t & 31)) & 1u) s += S.slot[((size_t)bb * amax + t) * 4 + comp];
+                    S.sd[it] = s;
+                }
+            }
+            if (args.want_force) {
+                const int nf = nproj > 1 ? 12 : 3;
+                for (int it = threadIdx.x; it < nfrc * nf; it += NC * 32) {
+                    const int fi = it / nf, i = it % nf;
+                    const int t = S.ftl[fi];
+                    double s = 0.0;
+                    for (int bb = 0; bb < NC; bb++)
+                        if ((S.ymask[bb * W + (t >> 5)] >> (t & 31)) & 1u)
+                            s += (double)S.fslot[((size_t)bb * fmax + fi) * 12 + i];
+                    const int lm = i / 3, d = i % 3;
+                    atomicAdd(args.A + ((((size_t)k * natom + S.rec[t].J) * nproj + lm) * 3 + d),
+                              S.chiq[4 * fi + lm] * args.Nnorm * s);
+                }
+            }
+            if (k == args.K) break;
+            __syncthreads();
+
+            // ---- KB term of Hhat v_k, from the dots ----
+            float w[NC];
+#pragma unroll
+            for (int c = 0; c < NC; c++) w[c] = 0.f;
+            for (int wd = 0; wd < W; wd++) {
+                unsigned msk = S.ymask[b * W + wd];
+                while (msk) {
+                    const int t = 32 * wd + __ffs(msk) - 1;
+                    msk &= msk - 1u;
+                    const float4 s = *reinterpret_cast<const float4 *>(S.sd + 4 * t);
+                    const float2 yv = S.tab[(t * 3 + 1) * NC + b];
+                    const float2 xv = live ? S.tab[(t * 3 + 0) * NC + lane] : make_float2(0.f, 0.f);
+                    // kappa_l chi (chi^T v) summed over s, p_x, p_y, p_z with the y factor folded in
+                    const float Pv = kap0 * s.x * yv.x + kap1 * s.z * yv.y;
+                    const float Qv = kap1 * s.w * yv.x;
+                    const float Rv = kap1 * s.y * yv.x;
+                    const float A1 = xv.x * Pv + xv.y * Rv;
+                    const float A2 = xv.x * Qv;
+                    const short lo = S.rec[t].lo[2], hi = S.rec[t].hi[2];
+                    const float2 *tz = S.tab + (t * 3 + 2) * NC;
+#pragma unroll
+                    for (int c0 = 0; c0 < NC; c0 += 4) {
+                        if (c0 + 3 < lo || c0 > hi) continue;
+#pragma unroll
+                        for (int cc = 0; cc < 4; cc++) {
+                            const int c = c0 + cc;
+                            if (c < NC) {
+                                const float2 z = tz[c];
+                                w[c] += z.x * A1 + z.y * A2;
+                            }
+                        }
+                    }
+                }
+            }
+            // ---- stencil + diagonal, w = ca Hhat v_k - cb v_{k-1} over v_{k-1} ----
+            const float ca = k == 0 ? 1.f : 2.f, cb = k == 0 ? 0.f : 1.f;
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+                const float x = vz[c];
+                float t = live ? drow[(size_t)c * plane_p] * x : 0.f;
+#pragma unroll
+                for (int j = 1; j <= P; j++) {
+                    const float zp = (c + j < NC) ? vz[c + j] : 0.f;
+                    const float zm = (c - j >= 0) ? vz[c - j] : 0.f;
+                    t += args.w[2][j - 1] * (zp + zm);
+                }
+#pragma unroll
+                for (int j = 1; j <= P; j++) {
+                    float xp = __shfl_down_sync(0xffffffffu, x, j);
+                    float xm = __shfl_up_sync(0xffffffffu, x, j);
+                    xp = (lane + j < NC) ? xp : 0.f;
+                    xm = (lane >= j) ? xm : 0.f;
+                    t += args.w[0][j - 1] * (xp + xm);
+                }
+                if (live) {
+                    const float *row = vcur + (size_t)(c * NC + b) * NC + lane;
+#pragma unroll
+                    for (int j = 1; j <= P; j++) {
+                        const float yp = (b + j < NC) ? row[j * NC] : 0.f;
+                        const float ym = (b - j >= 0) ? row[-j * NC] : 0.f;
+                        t += args.w[1][j - 1] * (yp + ym);
+                    }
+                    float *pv = vprev + (size_t)(c * NC + b) * NC + lane;
+                    const float nv = ca * (w[c] + t) - cb * (*pv);
+                    *pv = nv;
+                    w[c] = nv;
+                } else {
+                    w[c] = 0.f;
+                }
+            }
+            if (live && lane == m && b == m) args.mu[(size_t)(k + 1) * N_d + q] = w[m];
+            __syncthreads();
+            float *sw = vprev;
+            vprev = vcur;
+            vcur = sw;
+#pragma unroll
+            for (int c = 0; c < NC; c++) vz[c] = w[c];
+        }
+        __syncthreads();
+    }
+}
+
+template <int NC, int P>
+cudaError_t launch_nc(const RecursionArgs<float> &args, int amax, int fmax, int grid, size_t smem, int *err,
+                      cudaStream_t stream)
+{
+    auto kern = slab_kernel<NC, P>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NC * 32, smem, stream>>>(args, amax, fmax, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool slab_supported(const int nc[3], int fd_half)
+{
+    return nc[0] == nc[1] && nc[1] == nc[2] && (nc[0] == 21 || nc[0] == 25) && fd_half == 6;
+}
+
+size_t slab_smem_bytes(int nc, int amax, int fmax)
+{
+    switch (nc) {
+    case 21: return slab_layout<21>(nullptr, amax, fmax, nullptr);
+    case 25: return slab_layout<25>(nullptr, amax, fmax, nullptr);
+    default: return ~size_t(0);
+    }
+}
+
+cudaError_t slab_counts(const RecursionArgs<float> &args, int *d_counts, int num_sms, cudaStream_t stream)
+{
+    k_slab_counts<<<num_sms * 4, 128, 0, stream>>>(args, d_counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slab(const RecursionArgs<float> &args, int amax, int fmax, int grid, size_t smem, int *err,
+                        cudaStream_t stream)
+{
+    switch (args.nc[0]) {
+    case 21: return launch_nc<21, 6>(args, amax, fmax, grid, smem, err, stream);
+    case 25: return launch_nc<25, 6>(args, amax, fmax, grid, smem, err, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sq

@@ -176,6 +176,10 @@ def test_tiny_cell_fp32_within_stated_error(tiny):
 
 
 def test_vacancy_fp32_sampled_columns(vacancy):
+    """FP32 recursion (the 25^3 slab kernel) at full size: sampled moments against the oracle
+    (~1e-7 per moment: K = 60 steps of ~40-term FP32 sums), and lambda_f, U, forces and sampled rho
+    against the oracle's full-size golden values.  The energy and force tolerances are the paper's
+    accuracy targets (1e-4 Ha/atom, 1e-4 Ha/bohr; Sec. 4): the FP32 error must stay below them."""
     c, (lo, hi), _ = vacancy
     gpu = sq.solve_cell(c, sq.SQ_FP32, force=True, bounds=(lo, hi))
     omega, tau = oracle.scale_shift(lo, hi)
@@ -186,6 +190,31 @@ def test_vacancy_fp32_sampled_columns(vacancy):
     assert err < 5e-5
     dV = float(np.prod(c.h))
     assert abs(gpu["rho"].sum() * dV - c.N_e) < 1e-9 * c.N_e
+    path = os.path.join(GOLDEN, "vacancy_95atom.json")
+    if os.path.exists(path):
+        g = json.load(open(path))
+        idx = np.array(g["rho_idx"])
+        e = dict(dlam=abs(gpu["lam_f"] - g["lam_f"]), dU_atom=abs(gpu["U"] - g["U"]) / c.natom,
+                 rho_rel=float(np.max(np.abs(gpu["rho"][idx] - g["rho"])) / np.max(np.abs(g["rho"]))),
+                 df=float(np.max(np.abs(gpu["force"] - np.array(g["force"])))))
+        print("FP32 vacancy errors vs oracle", e)
+        assert e["dlam"] < 1e-5 and e["dU_atom"] < 1e-4 and e["rho_rel"] < 1e-4 and e["df"] < 1e-4
+
+
+def test_fp32_21_cube_matches_oracle():
+    """FP32 on a 21^3 cube (R_cut = 5 bohr, the batch workload's smallest truncation): sampled
+    moments of a 48-site cell against the oracle."""
+    c = cells.make_cell("rc5", (3, 2, 2), 0.5, 12, 1, 5.0, 24, 0.005, seed=9, n_vacancy=1)
+    assert np.all(c.n_c == 21)
+    lo, hi = oracle.spectral_bounds(c)
+    gpu = sq.solve_cell(c, sq.SQ_FP32, force=True, bounds=(lo, hi))
+    ref64 = sq.solve_cell(c, sq.SQ_FP64, force=True, bounds=(lo, hi))
+    omega, tau = oracle.scale_shift(lo, hi)
+    cols = cells.sample_columns(c, 24)
+    mu = oracle.moments(c, omega, tau, cols=cols)
+    assert float(np.max(np.abs(gpu["mu"][:, cols].T - mu))) < 2e-5
+    np.testing.assert_allclose(ref64["mu"][:, cols].T, mu, rtol=0, atol=1e-12)
+    assert abs(gpu["lam_f"] - ref64["lam_f"]) < 1e-5
 
 
 # ---------------------------------------------------------------------------------------------

@@ -13,7 +13,9 @@ pytestmark = pytest.mark.gpu
 
 from paper_2011_13517_gb300 import cells, sq  # noqa: E402
 
-ATOL = 1e-12   # the FP64 moment tolerance of the parity tests (|mu_k| <= 1)
+# the moment tolerances of the parity tests (|mu_k| <= 1): FP64 1e-12; FP32 5e-5 (sq_density may run
+# a different FP32 kernel, so the two FP32 results agree only to FP32 rounding)
+ATOL = {sq.SQ_FP64: 1e-12, sq.SQ_FP32: 5e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,7 +39,8 @@ def test_noalloc_moments_match_density_on_two_calls(cell_fn, K, precision):
         sq.sq_moments_noalloc(h, K, precision, out)
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
-        np.testing.assert_allclose(out.double().cpu().numpy(), ref.double().cpu().numpy(), rtol=0, atol=ATOL)
+        np.testing.assert_allclose(out.double().cpu().numpy(), ref.double().cpu().numpy(), rtol=0,
+                                   atol=ATOL[precision])
     h.close()
 
 
