@@ -222,6 +222,44 @@ long long sq_kernel_launches(void);
  */
 sq_status sq_moments_noalloc(sq_handle h, int K, int precision, void *d_mu, void *stream);
 
+/*
+ * Batched evaluation of many independent cells (the paper's method applied to a set of defect cells,
+ * Sec. 3 per cell): every cell's per-point recursion runs in ONE persistent kernel launch whose CTAs
+ * take (cell, column-range) work items from a queue, followed by each cell's moment sums, Fermi
+ * level, weights and density -- the whole sequence captured once into a CUDA graph and replayed.
+ *
+ * sq_batch_create -- group built handles (cells may differ in grid, cube, atoms, K, kT, N_e; they must
+ * share the FD order and the device).  Allocates every buffer the graph will use.
+ *   cells[ncells]   handles from sq_build_hamiltonian (owned by the caller; keep them alive)
+ *   K, kT, N_e      host [ncells] per-cell polynomial order, smearing and electron count
+ *   precision       SQ_FP64 or SQ_FP32;  flags: 0 or SQ_WANT_FORCE
+ * Errors: SQ_ERR_ARG, SQ_ERR_UNSUPPORTED, SQ_ERR_OOM, SQ_ERR_CUDA.
+ */
+typedef struct sq_batch_s *sq_batch;
+sq_status sq_batch_create(const sq_handle *cells, int ncells, const int *K, const double *kT, const double *N_e,
+                          int precision, int flags, sq_batch *out);
+
+/*
+ * sq_batch_density -- run the batch.  The first call autotunes the recursion launch (vectors in shared
+ * memory with 512 or 256 threads, or in global scratch; work items of 32, 128 or 512 columns), timed
+ * on a prefix of the work queue, then captures the graph; later calls with the same d_rho pointers
+ * replay it (new pointers trigger a new capture).  Afterwards each handle holds its cell's results as
+ * after sq_density, so sq_energy and sq_nonlocal_force apply per cell.
+ *   d_rho[ncells]   device FP64 density outputs, one per cell (caller-owned)
+ *   lambda_f        host [ncells] Fermi levels (may be NULL)
+ * Errors: SQ_ERR_ARG, SQ_ERR_NO_BRACKET, SQ_ERR_NOT_FINITE, SQ_ERR_UNSUPPORTED, SQ_ERR_CUDA.
+ * Synchronises `stream`.
+ */
+sq_status sq_batch_density(sq_batch b, double *const *d_rho, double *lambda_f, void *stream);
+
+/* Tuning and graph facts of a batch: chosen configuration (0: shared-memory vectors with 512
+ * threads, 1: with 256 threads, 2: global-scratch vectors), columns per work item, CTAs in the
+ * persistent launch, tuned probe time (ms) and number of graph nodes.  Any output may be NULL. */
+sq_status sq_batch_info(sq_batch b, int *config, int *chunk, int *grid, double *tuned_ms, long long *graph_nodes);
+
+/* Release a batch (NULL is ignored; the cell handles are not touched). */
+void sq_batch_destroy(sq_batch b);
+
 /* Release a handle and its device workspace (NULL is ignored).  Synchronises the device. */
 void sq_destroy(sq_handle h);
 

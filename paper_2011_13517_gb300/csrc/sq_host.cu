@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "sq_internal.h"
@@ -1177,4 +1178,418 @@ extern "C" sq_status sq_moments_noalloc(sq_handle h, int K, int precision, void 
     cudaStream_t stream = (cudaStream_t)stream_;
     return precision == SQ_FP64 ? moments_noalloc<double>(h, K, d_mu, stream)
                                 : moments_noalloc<float>(h, K, d_mu, stream);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Batched evaluation: many cells, one persistent recursion launch, a CUDA graph.
+
+// Fermi state initialised on the device (capturable: no host memory behind the copy)
+__global__ void k_fermi_init(FermiState *st, double lo, double hi)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        FermiState s;
+        memset(&s, 0, sizeof(s));
+        s.lo = lo;
+        s.hi = hi;
+        *st = s;
+    }
+}
+
+// node functions at the Fermi level held in the device state (valid once phase == 3)
+__global__ void k_node_functions_state(const double *lam, int M, const FermiState *st, double kT, double *fg,
+                                       double *flg, double *fs)
+{
+    if (st->phase != 3) return;
+    const double lam_f = st->x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+        const double l = lam[j];
+        const double g = fermi_fn(l, lam_f, kT);
+        const double y = fabs((l - lam_f) / kT);
+        fg[j] = g;
+        flg[j] = l * g;
+        fs[j] = -(log1p(exp(-y)) + y * fermi_fn(y, 0.0, 1.0));
+    }
+}
+
+constexpr int kBatchBisectSteps = 96;   // bisection launches captured in the graph (2 bracket + 94)
+
+struct sq_batch_s {
+    std::vector<sq_handle> cells;
+    std::vector<int> K, M;
+    std::vector<double> kT, N_e;
+    int precision = 0, want_force = 0, fd_half = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<double *> graph_rho;          // d_rho pointers the graph was captured with
+    void *d_cells = nullptr;                  // RecursionArgs<T> [ncells]
+    BatchItem *d_items = nullptr;
+    unsigned *d_counter = nullptr;
+    void *d_scratch = nullptr;
+    size_t scratch_cap = 0;
+    int nitems = 0, chunk = 0, config = -1, grid = 0, block = 0, vec_in_smem = 0;
+    size_t smem = 0;
+    long long scratch_stride = 0;
+    double tuned_ms = 0;
+    size_t graph_nodes = 0;
+    long long kernels_per_replay = 0;
+};
+
+template <typename T>
+static void fill_args(sq_handle h, int K, int want_force, RecursionArgs<T> &a)
+{
+    memset(&a, 0, sizeof(a));
+    for (int i = 0; i < 3; i++) {
+        a.n[i] = h->n[i];
+        a.m[i] = h->m[i];
+        a.nc[i] = h->nc[i];
+        a.pn[i] = h->pn[i];
+        a.fac_off[i] = h->fac2_off[i];
+        a.fac64_off[i] = h->fac64_off[i];
+        for (int j = 1; j <= h->p; j++) a.w[i][j - 1] = (T)(-h->fd[j] / (2.0 * h->h[i] * h->h[i] * h->tau));
+    }
+    a.nc3 = h->nc3;
+    a.N_d = h->N_d;
+    a.K = K;
+    a.natom = h->natom;
+    a.nproj = h->nproj;
+    a.want_force = want_force;
+    if constexpr (sizeof(T) == 8) {
+        a.dpad = reinterpret_cast<const T *>(h->d_dpad64);
+        a.fac = reinterpret_cast<const T *>(h->d_fac2_64);
+    } else {
+        a.dpad = reinterpret_cast<const T *>(h->d_dpad32);
+        a.fac = reinterpret_cast<const T *>(h->d_fac2_32);
+    }
+    a.kappa[0] = (T)(h->cl[0] * h->dV * h->Nnorm * h->Nnorm / h->tau);
+    a.kappa[1] = (T)(h->cl[1] * h->dV * h->Nnorm * h->Nnorm / h->tau);
+    a.fac_stride = h->fac2_stride;
+    a.fac64 = h->d_fac64;
+    a.fac64_stride = h->fac64_stride;
+    a.sup_start = h->d_sup;
+    a.sup_len = h->d_sup + 3 * (h->natom > 0 ? h->natom : 1);
+    a.Nnorm = h->Nnorm;
+    a.mu = reinterpret_cast<T *>(h->d_mu);
+    a.A = want_force ? h->d_A : nullptr;
+}
+
+extern "C" void sq_batch_destroy(sq_batch b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->d_cells);
+    cudaFree(b->d_items);
+    cudaFree(b->d_counter);
+    cudaFree(b->d_scratch);
+    delete b;
+}
+
+extern "C" sq_status sq_batch_create(const sq_handle *cells, int ncells, const int *K, const double *kT,
+                                     const double *N_e, int precision, int flags, sq_batch *out)
+{
+    g_last_error[0] = 0;
+    if (!cells || !K || !kT || !N_e || !out || ncells < 1) return fail(SQ_ERR_ARG, "null argument or ncells < 1");
+    if (precision != SQ_FP64 && precision != SQ_FP32) return fail(SQ_ERR_ARG, "precision %d", precision);
+    if (flags & ~SQ_WANT_FORCE) return fail(SQ_ERR_ARG, "flags %d", flags);
+    sq_batch_s *b = new sq_batch_s();
+    auto cleanup = [&](sq_status s) {
+        sq_batch_destroy(b);
+        return s;
+    };
+    b->precision = precision;
+    b->want_force = (flags & SQ_WANT_FORCE) ? 1 : 0;
+    for (int i = 0; i < ncells; i++) {
+        sq_handle h = cells[i];
+        if (!h) return cleanup(fail(SQ_ERR_ARG, "cell %d: null handle", i));
+        if (i > 0 && (h->p != cells[0]->p || h->dev != cells[0]->dev))
+            return cleanup(fail(SQ_ERR_UNSUPPORTED, "cell %d: all cells must share the FD order and device", i));
+        if (K[i] < 1 || K[i] > 4096 || !(kT[i] > 0) || !(N_e[i] > 0) || !(N_e[i] < 2.0 * h->N_d))
+            return cleanup(fail(SQ_ERR_ARG, "cell %d: K=%d kT=%g N_e=%g", i, K[i], kT[i], N_e[i]));
+        const double need = fmax(4.0 * (K[i] + 1), 16.0 * h->tau / kT[i]);
+        int M = 1;
+        while (M < need) M <<= 1;
+        if (M > (1 << 26)) return cleanup(fail(SQ_ERR_UNSUPPORTED, "cell %d: kT/tau too small", i));
+        b->cells.push_back(h);
+        b->K.push_back(K[i]);
+        b->kT.push_back(kT[i]);
+        b->N_e.push_back(N_e[i]);
+        b->M.push_back(M);
+    }
+    b->fd_half = cells[0]->p;
+    // every buffer the graph touches is allocated now, never during capture
+    const size_t esz = precision == SQ_FP64 ? 8 : 4;
+    size_t max_nc3 = 0;
+    int max_natom = 0;
+    int max_nc[3] = {0, 0, 0};
+    for (int i = 0; i < ncells; i++) {
+        sq_handle h = b->cells[i];
+        sq_status s;
+        const int Ki = b->K[i];
+        if ((s = ensure(&h->d_mu, &h->mu_bytes, esz * (size_t)(Ki + 1) * h->N_d))) return cleanup(s);
+        if ((s = ensure(&h->d_msum, &h->msum_cap, sizeof(double) * (size_t)(Ki + 1)))) return cleanup(s);
+        if ((s = ensure(&h->d_msum_part, &h->part_cap, sizeof(double) * (size_t)(Ki + 1) * kSumBlocks))) return cleanup(s);
+        if (b->want_force && h->natom > 0)
+            if ((s = ensure(&h->d_A, &h->A_cap, sizeof(double) * (size_t)(Ki + 1) * h->natom * h->nproj * 3))) return cleanup(s);
+        if ((s = ensure(&h->d_coef, &h->coef_cap, sizeof(double) * 3 * (size_t)(Ki + 1)))) return cleanup(s);
+        if ((s = ensure(&h->d_nodes, &h->nodes_cap, sizeof(double) * 5 * (size_t)b->M[i]))) return cleanup(s);
+        const size_t pad = (size_t)h->pn[0] * h->pn[1] * h->pn[2];
+        size_t cap = 0;
+        if (precision == SQ_FP64 && !h->d_dpad64) {
+            if ((s = ensure(&h->d_dpad64, &cap, sizeof(double) * pad))) return cleanup(s);
+        } else if (precision == SQ_FP32 && !h->d_dpad32) {
+            if ((s = ensure(&h->d_dpad32, &cap, sizeof(float) * pad))) return cleanup(s);
+        }
+        max_nc3 = std::max(max_nc3, (size_t)h->nc3);
+        max_natom = std::max(max_natom, h->natom);
+        for (int a = 0; a < 3; a++) max_nc[a] = std::max(max_nc[a], h->nc[a]);
+    }
+    int dev_smem = 0, num_sms = b->cells[0]->num_sms;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->cells[0]->dev);
+    SQ_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    SQ_CUDA(cudaMalloc(&b->d_cells, (precision == SQ_FP64 ? sizeof(RecursionArgs<double>) : sizeof(RecursionArgs<float>)) * ncells));
+    SQ_CUDA(cudaMalloc(&b->d_counter, 64));
+    // candidate configurations: vectors in shared memory (512 or 256 threads) or in global scratch
+    b->smem = 0;
+    const size_t smem_vec = precision == SQ_FP64 ? recursion_smem_bytes<double>(max_natom, max_nc, 1)
+                                                 : recursion_smem_bytes<float>(max_natom, max_nc, 1);
+    const size_t smem_glob = precision == SQ_FP64 ? recursion_smem_bytes<double>(max_natom, max_nc, 0)
+                                                  : recursion_smem_bytes<float>(max_natom, max_nc, 0);
+    if (smem_glob > (size_t)dev_smem) return cleanup(fail(SQ_ERR_UNSUPPORTED, "too many atoms for shared memory"));
+    b->scratch_stride = 2 * (long long)max_nc3;
+    const long long scratch_bytes = (long long)esz * b->scratch_stride * num_sms * 2;
+    SQ_CUDA(cudaMalloc(&b->d_scratch, scratch_bytes));
+    b->scratch_cap = scratch_bytes;
+    (void)smem_vec;
+    *out = b;
+    return SQ_OK;
+}
+
+template <typename T>
+static sq_status batch_enqueue(sq_batch b, double *const *d_rho, cudaStream_t stream, int config, int chunk,
+                               int limit_items, float *ms_out)
+{
+    const int nc = (int)b->cells.size();
+    int dev_smem = 0, num_sms = b->cells[0]->num_sms;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->cells[0]->dev);
+    int max_natom = 0, max_nc[3] = {0, 0, 0};
+    for (auto h : b->cells) {
+        max_natom = std::max(max_natom, h->natom);
+        for (int a = 0; a < 3; a++) max_nc[a] = std::max(max_nc[a], h->nc[a]);
+    }
+    BatchLaunch<T> L;
+    memset(&L, 0, sizeof(L));
+    L.vec_in_smem = config != 2;
+    L.block = config == 0 ? 512 : 256;
+    L.smem = recursion_smem_bytes<T>(max_natom, max_nc, L.vec_in_smem);
+    if (L.smem > (size_t)dev_smem) return fail(SQ_ERR_UNSUPPORTED, "configuration %d does not fit", config);
+    const int per_sm = batch_blocks_per_sm<T>(b->fd_half, L.block, L.smem, L.vec_in_smem);
+    if (per_sm < 1) return fail(SQ_ERR_UNSUPPORTED, "configuration %d does not fit on an SM", config);
+    L.grid = per_sm * num_sms;
+    if (!L.vec_in_smem && (size_t)L.grid * b->scratch_stride * sizeof(T) > b->scratch_cap)
+        L.grid = (int)(b->scratch_cap / (b->scratch_stride * sizeof(T)));
+    // work items: column chunks of every cell
+    std::vector<BatchItem> items;
+    for (int i = 0; i < nc; i++)
+        for (long long q = 0; q < b->cells[i]->N_d; q += chunk) items.push_back({i, 0, q, q + chunk});
+    int nitems = (int)items.size();
+    if (limit_items > 0 && nitems > limit_items) nitems = limit_items;
+    if (!b->d_items || b->nitems < (int)items.size() || b->chunk != chunk) {
+        if (b->d_items) cudaFree(b->d_items);
+        SQ_CUDA(cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size()));
+        SQ_CUDA(cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+        b->nitems = (int)items.size();
+        b->chunk = chunk;
+    }
+    L.cells = reinterpret_cast<const RecursionArgs<T> *>(b->d_cells);
+    L.items = b->d_items;
+    L.nitems = nitems;
+    L.counter = b->d_counter;
+    L.scratch = reinterpret_cast<T *>(b->d_scratch);
+    L.scratch_stride = b->scratch_stride;
+    b->grid = L.grid;
+    b->block = L.block;
+    b->vec_in_smem = L.vec_in_smem;
+    b->smem = L.smem;
+
+    // per-cell diagonal and force accumulators
+    for (int i = 0; i < nc; i++) {
+        sq_handle h = b->cells[i];
+        const size_t pad = (size_t)h->pn[0] * h->pn[1] * h->pn[2];
+        T *dp = sizeof(T) == 8 ? reinterpret_cast<T *>(h->d_dpad64) : reinterpret_cast<T *>(h->d_dpad32);
+        SQ_COUNT(1);
+        k_dpad<T><<<grid_for((long long)pad, 256, h->num_sms), 256, 0, stream>>>(
+            h->d_veff, h->n[0], h->n[1], h->n[2], h->m[0], h->m[1], h->m[2], h->kdiag, h->omega, h->tau, dp);
+        SQ_CUDA(cudaGetLastError());
+        if (b->want_force && h->natom > 0)
+            SQ_CUDA(cudaMemsetAsync(h->d_A, 0, sizeof(double) * (size_t)(b->K[i] + 1) * h->natom * h->nproj * 3, stream));
+    }
+    SQ_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms_out) {
+        SQ_CUDA(cudaEventCreate(&e0));
+        SQ_CUDA(cudaEventCreate(&e1));
+        SQ_CUDA(cudaEventRecord(e0, stream));
+    }
+    SQ_COUNT(1);
+    SQ_CUDA(launch_batch<T>(L, b->fd_half, stream));
+    if (ms_out) {
+        SQ_CUDA(cudaEventRecord(e1, stream));
+        SQ_CUDA(cudaEventSynchronize(e1));
+        SQ_CUDA(cudaEventElapsedTime(ms_out, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return SQ_OK;   // timing run of the recursion only
+    }
+    // per-cell moment sums, Fermi level (fixed number of bisection launches), weights and density
+    for (int i = 0; i < nc; i++) {
+        sq_handle h = b->cells[i];
+        const int K = b->K[i], M = b->M[i];
+        int *d_bad = reinterpret_cast<int *>(h->d_small);
+        SQ_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), stream));
+        dim3 g2(kSumBlocks, K + 1);
+        SQ_COUNT(2);
+        k_msum_partial<T><<<g2, 256, 0, stream>>>(reinterpret_cast<const T *>(h->d_mu), h->N_d, K, h->d_msum_part);
+        k_msum_final<<<1, 256, 0, stream>>>(h->d_msum_part, kSumBlocks, K, h->d_msum, d_bad);
+        SQ_CUDA(cudaGetLastError());
+        double *lam = h->d_nodes, *D = h->d_nodes + M, *f0 = h->d_nodes + 2 * M, *f1 = h->d_nodes + 3 * M,
+               *f2 = h->d_nodes + 4 * M;
+        FermiState *st = reinterpret_cast<FermiState *>(reinterpret_cast<char *>(h->d_small) + 256);
+        double *part = reinterpret_cast<double *>(reinterpret_cast<char *>(h->d_small) + 512);
+        SQ_COUNT(2 + kBatchBisectSteps);
+        k_nodes<<<grid_for(M, 256, h->num_sms), 256, 0, stream>>>(h->d_msum, K, M, h->omega, h->tau, lam, D);
+        k_fermi_init<<<1, 32, 0, stream>>>(st, h->lmin, h->lmax_);
+        for (int it = 0; it < kBatchBisectSteps; it++)
+            k_fermi_step<<<kFermiBlocks, 256, 0, stream>>>(lam, D, M, b->kT[i], b->N_e[i], st, part);
+        SQ_CUDA(cudaGetLastError());
+        SQ_COUNT(3);
+        k_node_functions_state<<<grid_for(M, 256, h->num_sms), 256, 0, stream>>>(lam, M, st, b->kT[i], f0, f1, f2);
+        k_coeffs<<<dim3(K + 1, 3), 256, 0, stream>>>(f0, f1, f2, M, K, h->d_coef);
+        k_density<T><<<grid_for(h->N_d, 256, h->num_sms), 256, 0, stream>>>(reinterpret_cast<const T *>(h->d_mu),
+                                                                           h->N_d, K, h->d_coef, 1.0 / h->dV, d_rho[i]);
+        SQ_CUDA(cudaGetLastError());
+    }
+    return SQ_OK;
+}
+
+template <typename T>
+static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, cudaStream_t stream)
+{
+    const int nc = (int)b->cells.size();
+    // device argument blocks of every cell
+    std::vector<RecursionArgs<T>> args(nc);
+    for (int i = 0; i < nc; i++) fill_args<T>(b->cells[i], b->K[i], b->want_force && b->cells[i]->natom > 0, args[i]);
+    SQ_CUDA(cudaMemcpy(b->d_cells, args.data(), sizeof(RecursionArgs<T>) * nc, cudaMemcpyHostToDevice));
+    // autotune once: kernel configuration x work-item size, timed on a prefix of the work queue
+    if (b->config < 0) {
+        SQ_CUDA(cudaStreamSynchronize(stream));
+        const int configs[3] = {0, 1, 2};
+        const int chunks[3] = {32, 128, 512};
+        float best = 1e30f;
+        int bc = -1, bk = 128;
+        for (int ci = 0; ci < 3; ci++)
+            for (int ki = 0; ki < 3; ki++) {
+                float ms = 0;
+                // each probe times the same number of columns: two per SM per work-item size, at most a
+                // sixth of the batch
+                long long total = 0;
+                for (auto h : b->cells) total += h->N_d;
+                long long cols = std::min<long long>((long long)b->cells[0]->num_sms * 2 * 512, total / 6);
+                const int probe = (int)std::max<long long>(1, cols / chunks[ki]);
+                if (batch_enqueue<T>(b, d_rho, b->cap_stream, configs[ci], chunks[ki], probe, &ms) != SQ_OK) continue;
+                if (ms < best) {
+                    best = ms;
+                    bc = configs[ci];
+                    bk = chunks[ki];
+                }
+            }
+        if (bc < 0) return fail(SQ_ERR_UNSUPPORTED, "no recursion configuration fits this batch");
+        b->config = bc;
+        b->chunk = -1;   // force the item table for the chosen chunk
+        b->tuned_ms = best;
+        b->nitems = 0;
+        g_last_error[0] = 0;
+        sq_status s = batch_enqueue<T>(b, d_rho, b->cap_stream, bc, bk, 1, &best);   // build the item table
+        if (s) return s;
+        b->chunk = bk;
+    }
+    bool same = b->exec && (int)b->graph_rho.size() == nc;
+    for (int i = 0; same && i < nc; i++) same = b->graph_rho[i] == d_rho[i];
+    if (!same) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        SQ_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const long long before = g_launches;
+        sq_status s = batch_enqueue<T>(b, d_rho, b->cap_stream, b->config, b->chunk, 0, nullptr);
+        b->kernels_per_replay = g_launches - before;
+        g_launches = before;
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &g);
+        if (s) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        SQ_CUDA(ce);
+        b->graph = g;
+        SQ_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+        SQ_CUDA(cudaGraphGetNodes(g, nullptr, &b->graph_nodes));
+        b->graph_rho.assign(d_rho, d_rho + nc);
+    }
+    SQ_CUDA(cudaGraphLaunch(b->exec, stream));
+    SQ_COUNT(b->kernels_per_replay);
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    // results and checks; a bisection that needs more than the captured steps continues here with the
+    // same rule (rare: the Fermi level within a few ulp of zero)
+    for (int i = 0; i < nc; i++) {
+        sq_handle h = b->cells[i];
+        int bad = 0;
+        FermiState fin;
+        FermiState *st = reinterpret_cast<FermiState *>(reinterpret_cast<char *>(h->d_small) + 256);
+        SQ_CUDA(cudaMemcpy(&bad, h->d_small, sizeof(int), cudaMemcpyDeviceToHost));
+        SQ_CUDA(cudaMemcpy(&fin, st, sizeof(fin), cudaMemcpyDeviceToHost));
+        if (bad) return fail(SQ_ERR_NOT_FINITE, "cell %d: moment sums are not finite", i);
+        if (fin.phase == 4)
+            return fail(SQ_ERR_NO_BRACKET, "cell %d: N(lambda_min) = %.6g, N(lambda_max) = %.6g, N_e = %.6g", i,
+                        fin.N_lo, fin.N_hi, b->N_e[i]);
+        h->precision = b->precision;
+        h->K = b->K[i];
+        if (fin.phase != 3) {
+            sq_status s = fermi_and_density(h, b->kT[i], b->N_e[i], d_rho[i], &fin.x, stream);
+            if (s) return s;
+        }
+        h->kT = b->kT[i];
+        h->N_e = b->N_e[i];
+        h->lam_f = fin.x;
+        h->M = b->M[i];
+        h->have_force = b->want_force && h->natom > 0;
+        h->have_density = 1;
+        if (lambda_f) lambda_f[i] = fin.x;
+    }
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_batch_density(sq_batch b, double *const *d_rho, double *lambda_f, void *stream_)
+{
+    g_last_error[0] = 0;
+    if (!b || !d_rho) return fail(SQ_ERR_ARG, "null argument");
+    for (size_t i = 0; i < b->cells.size(); i++)
+        if (!d_rho[i]) return fail(SQ_ERR_ARG, "cell %zu: null density buffer", i);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    return b->precision == SQ_FP64 ? batch_run<double>(b, d_rho, lambda_f, stream)
+                                   : batch_run<float>(b, d_rho, lambda_f, stream);
+}
+
+extern "C" sq_status sq_batch_info(sq_batch b, int *config, int *chunk, int *grid, double *tuned_ms, long long *graph_nodes)
+{
+    if (!b) return fail(SQ_ERR_ARG, "null batch");
+    if (config) *config = b->config;
+    if (chunk) *chunk = b->chunk;
+    if (grid) *grid = b->grid;
+    if (tuned_ms) *tuned_ms = b->tuned_ms;
+    if (graph_nodes) *graph_nodes = (long long)b->graph_nodes;
+    return SQ_OK;
 }

@@ -48,6 +48,30 @@ struct RecursionArgs {
     int vec_in_smem;
 };
 
+// One work item of a batched launch: columns [begin, end) of cell `cell`.
+struct BatchItem {
+    int cell;
+    int pad;
+    long long begin, end;
+};
+
+template <typename T>
+struct BatchLaunch {
+    const RecursionArgs<T> *cells;   // device [ncells]
+    const BatchItem *items;          // device [nitems]
+    int nitems;
+    unsigned *counter;               // device, zero before the launch
+    T *scratch;                      // per-CTA vectors when !vec_in_smem
+    long long scratch_stride;        // elements per CTA
+    int grid, block, vec_in_smem;
+    size_t smem;
+};
+
+template <typename T>
+cudaError_t launch_batch(const BatchLaunch<T> &b, int fd_half, cudaStream_t stream);
+template <typename T>
+int batch_blocks_per_sm(int fd_half, int block, size_t smem, int vec_in_smem);
+
 // Launch the per-column recursion for all N_d columns.  Returns cudaSuccess or the launch error.
 template <typename T>
 cudaError_t launch_recursion(const RecursionArgs<T> &args, int fd_half, int grid, int block,

@@ -73,10 +73,12 @@ __device__ int block_compact(bool flag, int *scan, int *total)
     return slot;
 }
 
+// Columns q_begin, q_begin + q_step, ... < q_end of one cell, processed by the calling CTA.
+// smem_raw is the CTA's dynamic shared memory; scratch its two cube vectors when !VSMEM.
 template <typename T, int P, int BLOCK, bool VSMEM>
-__global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 2 : 1) recursion_kernel(const RecursionArgs<T> args)
+__device__ __forceinline__ void column_range(const RecursionArgs<T> &args, long long q_begin, long long q_end,
+                                             long long q_step, unsigned char *smem_raw, T *scratch)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int natom = args.natom;
     const int ncx = args.nc[0], ncy = args.nc[1], ncz = args.nc[2];
     const int nc3 = args.nc3;
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 2 : 1) recursion_kernel(
         va = vec;
         vb = vec + nc3;
     } else {
-        va = args.scratch + (size_t)blockIdx.x * 2 * nc3;
+        va = scratch;
         vb = va + nc3;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 2 : 1) recursion_kernel(
     const int nseg = nsx * ncy * ncz;
     const size_t plane_p = (size_t)args.pn[0] * args.pn[1];
 
-    for (long long q = blockIdx.x; q < N_d; q += gridDim.x) {
+    for (long long q = q_begin; q < q_end; q += q_step) {
         const int q1 = (int)(q % args.n[0]);
         const int q2 = (int)((q / args.n[0]) % args.n[1]);
         const int q3 = (int)(q / ((long long)args.n[0] * args.n[1]));
@@ -411,6 +413,36 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 2 : 1) recursion_kernel(
 }
 
 template <typename T, int P, int BLOCK, bool VSMEM>
+__global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 2 : 1) recursion_kernel(const RecursionArgs<T> args)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    column_range<T, P, BLOCK, VSMEM>(args, blockIdx.x, args.N_d, gridDim.x, smem_raw,
+                                     VSMEM ? nullptr : args.scratch + (size_t)blockIdx.x * 2 * args.nc3);
+}
+
+// Many cells in one persistent launch: each CTA takes (cell, column range) work items from a queue
+// (one atomicAdd per item; no CTA ever waits on another) until the queue is empty.
+template <typename T, int P, int BLOCK, bool VSMEM>
+__global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 2 : 1)
+    batch_kernel(const RecursionArgs<T> *cells, const BatchItem *items, int nitems, unsigned *counter, T *scratch,
+                 long long scratch_stride)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int item_s;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = item_s;
+        __syncthreads();
+        if (it >= nitems) break;
+        const BatchItem w = items[it];
+        const RecursionArgs<T> a = cells[w.cell];
+        column_range<T, P, BLOCK, VSMEM>(a, w.begin, w.end < a.N_d ? w.end : a.N_d, 1, smem_raw,
+                                         VSMEM ? nullptr : scratch + (size_t)blockIdx.x * scratch_stride);
+    }
+}
+
+template <typename T, int P, int BLOCK, bool VSMEM>
 cudaError_t launch_cfg(const RecursionArgs<T> &args, int grid, size_t smem, cudaStream_t stream)
 {
     auto kern = recursion_kernel<T, P, BLOCK, VSMEM>;
@@ -444,6 +476,42 @@ int blocks_p(int block, size_t smem, int vec_in_smem)
 {
     if (vec_in_smem) return block == 512 ? blocks_cfg<T, P, 512, true>(smem) : blocks_cfg<T, P, 256, true>(smem);
     return blocks_cfg<T, P, 256, false>(smem);
+}
+
+template <typename T, int P, int BLOCK, bool VSMEM>
+cudaError_t launch_batch_cfg(const BatchLaunch<T> &b, cudaStream_t stream)
+{
+    auto kern = batch_kernel<T, P, BLOCK, VSMEM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<b.grid, BLOCK, b.smem, stream>>>(b.cells, b.items, b.nitems, b.counter, b.scratch, b.scratch_stride);
+    return cudaGetLastError();
+}
+
+template <typename T, int P, int BLOCK, bool VSMEM>
+int batch_blocks_cfg(size_t smem)
+{
+    auto kern = batch_kernel<T, P, BLOCK, VSMEM>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, BLOCK, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+template <typename T, int P>
+cudaError_t launch_batch_p(const BatchLaunch<T> &b, cudaStream_t stream)
+{
+    if (b.vec_in_smem) return b.block == 512 ? launch_batch_cfg<T, P, 512, true>(b, stream)
+                                             : launch_batch_cfg<T, P, 256, true>(b, stream);
+    return launch_batch_cfg<T, P, 256, false>(b, stream);
+}
+
+template <typename T, int P>
+int batch_blocks_p(int block, size_t smem, int vec_in_smem)
+{
+    if (vec_in_smem) return block == 512 ? batch_blocks_cfg<T, P, 512, true>(smem)
+                                         : batch_blocks_cfg<T, P, 256, true>(smem);
+    return batch_blocks_cfg<T, P, 256, false>(smem);
 }
 
 }  // namespace
@@ -493,6 +561,24 @@ int recursion_blocks_per_sm(int fd_half, int block, size_t smem, int vec_in_smem
     return 0;
 }
 
+template <typename T>
+cudaError_t launch_batch(const BatchLaunch<T> &b, int fd_half, cudaStream_t stream)
+{
+    SQ_DISPATCH_P(launch_batch_p, b, stream)
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+int batch_blocks_per_sm(int fd_half, int block, size_t smem, int vec_in_smem)
+{
+    SQ_DISPATCH_P(batch_blocks_p, block, smem, vec_in_smem)
+    return 0;
+}
+
+template cudaError_t launch_batch<double>(const BatchLaunch<double> &, int, cudaStream_t);
+template cudaError_t launch_batch<float>(const BatchLaunch<float> &, int, cudaStream_t);
+template int batch_blocks_per_sm<double>(int, int, size_t, int);
+template int batch_blocks_per_sm<float>(int, int, size_t, int);
 template cudaError_t launch_recursion<double>(const RecursionArgs<double> &, int, int, int, size_t, cudaStream_t);
 template cudaError_t launch_recursion<float>(const RecursionArgs<float> &, int, int, int, size_t, cudaStream_t);
 template size_t recursion_smem_bytes<double>(int, const int *, int);

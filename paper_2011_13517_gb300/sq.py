@@ -26,7 +26,8 @@ STATUS = {0: "SQ_OK", 1: "SQ_ERR_ARG", 2: "SQ_ERR_CUBE_EXCEEDS_BOX", 3: "SQ_ERR_
 
 EXPORTS = ["sq_build_hamiltonian", "sq_density", "sq_fermi_level", "sq_energy", "sq_nonlocal_force",
            "sq_get_spectral_bounds", "sq_get_moments", "sq_copy_moments", "sq_get_cube", "sq_get_timing",
-           "sq_kernel_launches", "sq_moments_noalloc", "sq_destroy", "sq_status_string", "sq_last_error"]
+           "sq_kernel_launches", "sq_moments_noalloc", "sq_batch_create", "sq_batch_density", "sq_batch_info",
+           "sq_batch_destroy", "sq_destroy", "sq_status_string", "sq_last_error"]
 
 
 class SQError(RuntimeError):
@@ -70,13 +71,19 @@ def lib():
         L.sq_get_timing.argtypes = [vp, dp, dp, dp]
         L.sq_kernel_launches.argtypes = []
         L.sq_moments_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
+        L.sq_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, dp,
+                                      ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+        L.sq_batch_density.argtypes = [vp, ctypes.POINTER(vp), dp, vp]
+        L.sq_batch_info.argtypes = [vp, ip, ip, ip, dp, ctypes.POINTER(ctypes.c_longlong)]
+        L.sq_batch_destroy.argtypes = [vp]
+        L.sq_batch_destroy.restype = None
         L.sq_destroy.argtypes = [vp]
         L.sq_destroy.restype = None
         L.sq_status_string.argtypes = [ctypes.c_int]
         L.sq_status_string.restype = ctypes.c_char_p
         L.sq_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("sq_destroy", "sq_status_string", "sq_last_error", "sq_kernel_launches"):
+            if name not in ("sq_destroy", "sq_status_string", "sq_last_error", "sq_kernel_launches", "sq_batch_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         L.sq_kernel_launches.restype = ctypes.c_longlong
         _lib = L
@@ -193,6 +200,59 @@ def sq_moments_noalloc(h: Handle, K, precision, d_mu, stream=None):
     scratch array and its rules."""
     dt = torch.float64 if precision == SQ_FP64 else torch.float32
     _check(lib().sq_moments_noalloc(h.ptr, int(K), int(precision), _dev_ptr(d_mu, dt), _stream(stream)))
+
+
+class Batch:
+    """Owns an sq_batch (the cell handles stay owned by the caller and must outlive it)."""
+
+    def __init__(self, ptr, handles):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.handles = handles
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            lib().sq_batch_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+
+def sq_batch_create(handles, K, kT, N_e, precision, flags) -> Batch:
+    n = len(handles)
+    arr = (ctypes.c_void_p * n)(*[h.ptr.value for h in handles])
+    Ks = (ctypes.c_int * n)(*[int(x) for x in K])
+    kTs = np.ascontiguousarray(kT, dtype=np.float64)
+    Nes = np.ascontiguousarray(N_e, dtype=np.float64)
+    out = ctypes.c_void_p()
+    _check(lib().sq_batch_create(arr, n, Ks, kTs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 Nes.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(precision), int(flags),
+                                 ctypes.byref(out)))
+    return Batch(out.value, list(handles))
+
+
+def sq_batch_density(b: Batch, d_rhos, stream=None):
+    n = len(b.handles)
+    ptrs = (ctypes.c_void_p * n)(*[_dev_ptr(r).value for r in d_rhos])
+    lam = np.zeros(n)
+    _check(lib().sq_batch_density(b.ptr, ptrs, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
+    return lam
+
+
+def sq_batch_destroy(b: Batch):
+    b.close()
+
+
+def sq_destroy(h: Handle):
+    h.close()
+
+
+def sq_batch_info(b: Batch):
+    cfg, chunk, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms, nodes = ctypes.c_double(), ctypes.c_longlong()
+    _check(lib().sq_batch_info(b.ptr, ctypes.byref(cfg), ctypes.byref(chunk), ctypes.byref(grid), ctypes.byref(ms),
+                               ctypes.byref(nodes)))
+    return dict(config=cfg.value, chunk=chunk.value, grid=grid.value, tuned_ms=ms.value, graph_nodes=nodes.value)
 
 
 def sq_copy_moments(h: Handle, N_d, stream=None):

@@ -1,0 +1,79 @@
+"""Batched evaluation (one persistent recursion launch over several cells, CUDA graph, autotuned
+launch configuration) against the single-cell path and the oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle  # noqa: E402
+from paper_2011_13517_gb300 import cells, sq  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def small_batch():
+    """Cells of uneven size, cube and order: the tiny cell and three 48-site defect cells with
+    R_cut 5, 6 and 7 bohr (21^3, 25^3, 29^3 cubes) and K 12-24 (short, to keep the test quick)."""
+    out = [cells.tiny_cell()]
+    for i, (rc, K, nvac, nal) in enumerate([(5.0, 16, 1, 0), (6.0, 12, 0, 1), (7.0, 24, 2, 1)]):
+        out.append(cells.make_cell(f"b{i}", (3, 2, 2), 0.5, 12, 1, rc, K, 0.005, seed=40 + i,
+                                   n_vacancy=nvac, n_al=nal))
+    return out
+
+
+@pytest.mark.parametrize("precision", [sq.SQ_FP64, sq.SQ_FP32])
+def test_batch_matches_single_cell_path_and_replays(precision):
+    cs = small_batch()
+    # the tiny cell uses the 6th-order stencil; a batch shares one FD order, so it runs on its own
+    for group in ([cs[0]], cs[1:]):
+        handles = [sq.build_for_cell(c) for c in group]
+        b = sq.sq_batch_create(handles, [c.K for c in group], [c.kT for c in group], [c.N_e for c in group],
+                               precision, sq.SQ_WANT_FORCE)
+        rhos = [torch.empty(c.N_d, dtype=torch.float64, device="cuda") for c in group]
+        lam = sq.sq_batch_density(b, rhos)
+        info = sq.sq_batch_info(b)
+        assert info["graph_nodes"] > 0 and info["config"] in (0, 1, 2)
+        got = []
+        for h, c, r in zip(handles, group, rhos):
+            U, S, F = sq.sq_energy(h)
+            f = torch.empty((c.natom, 3), dtype=torch.float64, device="cuda")
+            sq.sq_nonlocal_force(h, f)
+            got.append((r.cpu().numpy(), U, f.cpu().numpy()))
+        # second call replays the same graph
+        lam2 = sq.sq_batch_density(b, rhos)
+        assert np.array_equal(lam, lam2)
+        for i, (c, r) in enumerate(zip(group, rhos)):
+            assert np.array_equal(r.cpu().numpy(), got[i][0])
+            ref = sq.solve_cell(c, precision, force=True)
+            tol = 1e-12 if precision == sq.SQ_FP64 else 1e-5
+            assert abs(lam[i] - ref["lam_f"]) < tol
+            rs = np.max(np.abs(ref["rho"]))
+            np.testing.assert_allclose(got[i][0], ref["rho"], rtol=0, atol=(1e-10 if precision == sq.SQ_FP64 else 1e-4) * rs)
+            assert abs(got[i][1] - ref["U"]) < (1e-10 if precision == sq.SQ_FP64 else 1e-4) * max(1.0, abs(ref["U"]))
+            fs = max(np.max(np.abs(ref["force"])), 1e-12)
+            np.testing.assert_allclose(got[i][2], ref["force"], rtol=0,
+                                       atol=(1e-9 * fs if precision == sq.SQ_FP64 else 1e-4))
+        b.close()
+        for h in handles:
+            h.close()
+
+
+def test_batch_fp64_sampled_columns_match_oracle():
+    """FP64 batch moments of the 29^3-cube cell against the oracle, column by column."""
+    cs = small_batch()[1:]
+    handles = [sq.build_for_cell(c, bounds=oracle.spectral_bounds(c)) for c in cs]
+    b = sq.sq_batch_create(handles, [c.K for c in cs], [c.kT for c in cs], [c.N_e for c in cs], sq.SQ_FP64, 0)
+    rhos = [torch.empty(c.N_d, dtype=torch.float64, device="cuda") for c in cs]
+    sq.sq_batch_density(b, rhos)
+    for h, c in zip(handles, cs):
+        mu, _ = sq.sq_copy_moments(h, c.N_d)
+        omega, tau = oracle.scale_shift(*oracle.spectral_bounds(c))
+        cols = cells.sample_columns(c, 8)
+        ref = oracle.moments(c, omega, tau, cols=cols)
+        np.testing.assert_allclose(mu.cpu().numpy()[:, cols].T, ref, rtol=0, atol=1e-12)
+    b.close()
