@@ -223,6 +223,25 @@ long long sq_kernel_launches(void);
 sq_status sq_moments_noalloc(sq_handle h, int K, int precision, void *d_mu, void *stream);
 
 /*
+ * sq_density_vjp -- vector-Jacobian product of the last sq_density: for the scalar
+ * L = sum_q rho_bar(x_q) rho(x_q) + U_bar U, writes d_veff_bar(x) = dL/dV_eff(x) on every grid point.
+ * The derivative includes the implicit change of the Fermi level (N(lambda_f) = N_e, Eq. Ne) and holds
+ * the scale and shift omega, tau fixed.  It runs the reverse (adjoint) Chebyshev recursion of every
+ * column -- a_K = mubar_K e_q, a_k = 2 Hhat_q a_{k+1} - a_{k+2} + mubar_k e_q (reverse Clenshaw) --
+ * with the forward vectors stored as checkpoint pairs every checkpoint_k steps and recomputed segment
+ * by segment (Eq. Chebyshev run backwards; the paper needs this derivative only implicitly, through
+ * the SCF mixing of V_eff, Sec. 3).  Same recursion precision as the last sq_density.
+ *   d_rho_bar    device [N_d] FP64 cotangent of rho (per bohr^3 density, as returned by sq_density)
+ *   U_bar        cotangent of the band energy U
+ *   checkpoint_k 1 <= checkpoint_k <= K (1: every vector kept; larger: less memory, more recompute)
+ *   d_veff_bar   device [N_d] FP64 output (overwritten)
+ * Column contributions are summed with FP64 atomics, so results may differ in the last bits between
+ * runs.  Errors: SQ_ERR_STATE (no sq_density), SQ_ERR_ARG, SQ_ERR_OOM, SQ_ERR_CUDA.  Synchronises `stream`.
+ */
+sq_status sq_density_vjp(sq_handle h, const double *d_rho_bar, double U_bar, int checkpoint_k,
+                         double *d_veff_bar, void *stream);
+
+/*
  * Batched evaluation of many independent cells (the paper's method applied to a set of defect cells,
  * Sec. 3 per cell): every cell's per-point recursion runs in ONE persistent kernel launch whose CTAs
  * take (cell, column-range) work items from a queue, followed by each cell's moment sums, Fermi

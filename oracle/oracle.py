@@ -71,6 +71,8 @@ def lib():
         _lib.sq_oracle_moments.argtypes = [ctypes.POINTER(_Problem), ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int, ctypes.c_long, lp, dp, dp, ctypes.c_int]
         _lib.sq_oracle_max_threads.restype = ctypes.c_int
+        _lib.sq_oracle_tangent.argtypes = [ctypes.POINTER(_Problem), ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                           dp, ctypes.c_long, lp, dp, ctypes.c_int]
     return _lib
 
 
@@ -387,3 +389,42 @@ def sq_solve(cell, force=True, bounds=None, nthreads=0, full=False, K=None, cols
         out["A"] = A
         out["force"] = nonlocal_force(A, c, cell.proj_energy, dV)
     return out
+
+
+# --------------------------------------------------------------------------------------------
+# Forward-mode derivative (tangent) of rho and U along a potential perturbation
+
+def moment_tangent(cell, omega, tau, dV, K=None, cols=None, nthreads=0):
+    """dmu [ncols, K+1]: derivative of the moments along dV (full grid), omega and tau fixed."""
+    K = cell.K if K is None else K
+    cols = np.arange(cell.N_d, dtype=np.int64) if cols is None else np.ascontiguousarray(cols, dtype=np.int64)
+    prob = Problem(cell)
+    dVa = np.ascontiguousarray(np.asarray(dV, dtype=np.float64).reshape(-1))
+    dmu = np.zeros((cols.size, K + 1))
+    rc = lib().sq_oracle_tangent(ctypes.byref(prob.st), float(omega), float(tau), int(K), _dp(dVa),
+                                 int(cols.size), _lp(cols), _dp(dmu), int(nthreads))
+    if rc:
+        raise RuntimeError(f"sq_oracle_tangent failed ({rc})")
+    return dmu
+
+
+def sq_tangent(cell, dV, bounds=None, K=None):
+    """(d rho [N_d], d U, d lambda_f) along dV: the moment tangent pushed through the weights with the
+    implicit derivative of the Fermi level, d lambda_f = -dN / N'(lambda_f), N = 2 sum_k c_k M_k
+    (Eq. Ne), N' = 2 sum_k c'_k M_k where c'_k are the Chebyshev weights of dg/dlambda_f."""
+    r = sq_solve(cell, force=False, bounds=bounds, K=K)
+    K = r["K"]
+    dmu = moment_tangent(cell, r["omega"], r["tau"], dV, K=K)
+    dM = dmu.sum(axis=0)
+    theta, x = cheb_nodes(r["M"])
+    lam = r["tau"] * x + r["omega"]
+    g = fermi(lam, r["lam_f"], cell.kT)
+    gp = g * (1.0 - g) / cell.kT
+    cp = cheb_coeffs(gp, theta, K)
+    dp = cheb_coeffs(lam * gp, theta, K)
+    Np = 2.0 * float(np.dot(cp, r["Msum"]))
+    dN = 2.0 * float(np.dot(r["c"], dM))
+    dlam = -dN / Np
+    drho = 2.0 * (dmu @ r["c"] + dlam * (r["mu"] @ cp)) / r["dV"]
+    dU = 2.0 * (float(np.dot(r["d"], dM)) + dlam * float(np.dot(dp, r["Msum"])))
+    return drho, dU, dlam, r

@@ -512,3 +512,91 @@ int sq_oracle_max_threads(void)
     return 1;
 #endif
 }
+
+/*
+ * Forward-mode tangent of the moments along a potential perturbation dV (full grid, FP64):
+ * differentiating Eq. Chebyshev with Hhat_q depending on V_eff through its diagonal,
+ *   dv_0 = 0,  dv_1 = dH v_0,  dv_{k+1} = 2 Hhat dv_k + 2 dH v_k - dv_{k-1},
+ * with dH = diag(dV restricted to the cube) / tau, and dmu_k^q = dv_k(q).  omega and tau are held
+ * fixed.  dmu is [ncols][K+1].
+ */
+int sq_oracle_tangent(const sq_oracle_problem *P, double omega, double tau, int K, const double *dV, long ncols,
+                      const long *cols, double *dmu, int nthreads)
+{
+    oracle_ctx C;
+    int rc = ctx_init(&C, P);
+    if (rc) return rc;
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel
+    {
+        double *v0 = (double *)malloc(sizeof(double) * C.nc3), *v1 = (double *)malloc(sizeof(double) * C.nc3);
+        double *d0 = (double *)malloc(sizeof(double) * C.nc3), *d1 = (double *)malloc(sizeof(double) * C.nc3);
+        double *t1 = (double *)malloc(sizeof(double) * C.nc3), *t2 = (double *)malloc(sizeof(double) * C.nc3);
+        double *dloc = (double *)malloc(sizeof(double) * C.nc3);
+        if (!v0 || !v1 || !d0 || !d1 || !t1 || !t2 || !dloc) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (long ic = 0; ic < ncols; ic++) {
+                long q = cols[ic];
+                int q3[3];
+                unravel(P, q, q3);
+                column_atoms ca;
+                if (column_atoms_build(&C, q3, &ca)) {
+#pragma omp atomic write
+                    err = 1;
+                    continue;
+                }
+                for (int c = 0; c < C.nc[2]; c++)
+                    for (int b = 0; b < C.nc[1]; b++)
+                        for (int a = 0; a < C.nc[0]; a++) {
+                            long lc = a + (long)C.nc[0] * (b + (long)C.nc[1] * c);
+                            long g = glob(&C, 0, q3[0], a) +
+                                     (long)P->n[0] * (glob(&C, 1, q3[1], b) + (long)P->n[1] * glob(&C, 2, q3[2], c));
+                            dloc[lc] = dV[g] / tau;
+                        }
+                const long cen = centre_local(&C);
+                double *vprev = v0, *vcur = v1, *dprev = d0, *dcur = d1;
+                double *mq = dmu + ic * (K + 1);
+                memset(vcur, 0, sizeof(double) * C.nc3);
+                vcur[cen] = 1.0;
+                memset(vprev, 0, sizeof(double) * C.nc3);
+                memset(dcur, 0, sizeof(double) * C.nc3);
+                memset(dprev, 0, sizeof(double) * C.nc3);
+                mq[0] = 0.0;
+                for (int k = 0; k < K; k++) {
+                    apply_hhat(&C, q3, &ca, omega, tau, vcur, t1);
+                    apply_hhat(&C, q3, &ca, omega, tau, dcur, t2);
+                    if (k == 0) {
+                        for (long i = 0; i < C.nc3; i++) {
+                            dprev[i] = t2[i] + dloc[i] * vcur[i];
+                            vprev[i] = t1[i];
+                        }
+                    } else {
+                        for (long i = 0; i < C.nc3; i++) {
+                            dprev[i] = 2.0 * t2[i] + 2.0 * dloc[i] * vcur[i] - dprev[i];
+                            vprev[i] = 2.0 * t1[i] - vprev[i];
+                        }
+                    }
+                    double *sw = vprev;
+                    vprev = vcur;
+                    vcur = sw;
+                    sw = dprev;
+                    dprev = dcur;
+                    dcur = sw;
+                    mq[k + 1] = dcur[cen];
+                }
+                column_atoms_free(&ca);
+            }
+        }
+        free(v0); free(v1); free(d0); free(d1); free(t1); free(t2); free(dloc);
+    }
+    ctx_free(&C);
+    return err ? -4 : 0;
+}

@@ -1593,3 +1593,128 @@ extern "C" sq_status sq_batch_info(sq_batch b, int *config, int *chunk, int *gri
     if (graph_nodes) *graph_nodes = (long long)b->graph_nodes;
     return SQ_OK;
 }
+
+// ------------------------------------------------------------------------------------------------
+// Vector-Jacobian product of (rho, U) with respect to V_eff (reverse mode through the recursion).
+
+// derivative functions at the Fermi level: dg/dlambda_f = g (1 - g)/kT, and lam * dg/dlambda_f
+__global__ void k_node_deriv(const double *lam, int M, double lam_f, double kT, double *f0, double *f1)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+        const double g = fermi_fn(lam[j], lam_f, kT);
+        const double gp = g * (1.0 - g) / kT;
+        f0[j] = gp;
+        f1[j] = lam[j] * gp;
+    }
+}
+
+// R_k = sum_q rhobar_q mu_k^q (partial sums per block, then k_msum_final)
+template <typename T>
+__global__ void k_wsum_partial(const T *mu, const double *w, long long N_d, int K, double *part)
+{
+    const int k = blockIdx.y;
+    double s = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N_d; q += (long long)gridDim.x * blockDim.x)
+        s += w[q] * (double)mu[(size_t)k * N_d + q];
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int wd = 0; wd < (int)(blockDim.x >> 5); wd++) t += red[wd];
+        part[(size_t)k * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// cotangent of the moments: mubar_k^q = alpha_k rhobar_q + beta_k with
+//   alpha_k = 2 c_k / dV,  beta_k = 2 Ubar d_k - 2 c_k lambar / N',
+//   N' = 2 sum c'_k M_k,  lambar = (2/dV) sum_k c'_k R_k + 2 Ubar sum_k d'_k M_k
+// (implicit derivative of the Fermi level through N(lambda_f) = N_e, Eq. Ne)
+__global__ void k_adj_scalars(const double *coef, const double *coefd, const double *msum, const double *R, int K,
+                              double inv_dV, double Ubar, double *alpha, double *beta, double *diag)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double *c = coef, *d = coef + (K + 1);
+    const double *cp = coefd, *dp = coefd + (K + 1);
+    double Np = 0.0, lr = 0.0, ld = 0.0;
+    for (int k = 0; k <= K; k++) {
+        Np += cp[k] * msum[k];
+        lr += cp[k] * R[k];
+        ld += dp[k] * msum[k];
+    }
+    Np *= 2.0;
+    const double lambar = 2.0 * inv_dV * lr + 2.0 * Ubar * ld;
+    for (int k = 0; k <= K; k++) {
+        alpha[k] = 2.0 * c[k] * inv_dV;
+        beta[k] = 2.0 * Ubar * d[k] - 2.0 * c[k] * lambar / Np;
+    }
+    diag[0] = Np;
+    diag[1] = lambar;
+}
+
+template <typename T>
+static sq_status density_vjp(sq_handle h, const double *d_rho_bar, double U_bar, int kc, double *d_vbar,
+                             cudaStream_t stream)
+{
+    const int K = h->K, M = h->M;
+    sq_status s;
+    // scratch: c', d' coefficients, R, alpha, beta
+    double *d_aux = nullptr;
+    size_t aux_cap = 0;
+    const size_t aux = sizeof(double) * (size_t)(5 * (K + 1) + 8);
+    if ((s = ensure(&d_aux, &aux_cap, aux))) return s;
+    double *coefd = d_aux, *R = coefd + 2 * (K + 1), *alpha = R + (K + 1), *beta = alpha + (K + 1),
+           *diag = beta + (K + 1);
+    double *lam = h->d_nodes, *f0 = h->d_nodes + 2 * M, *f1 = h->d_nodes + 3 * M;
+    SQ_COUNT(2);
+    k_node_deriv<<<grid_for(M, 256, h->num_sms), 256, 0, stream>>>(lam, M, h->lam_f, h->kT, f0, f1);
+    k_coeffs<<<dim3(K + 1, 2), 256, 0, stream>>>(f0, f1, f1, M, K, coefd);
+    dim3 g2(kSumBlocks, K + 1);
+    SQ_COUNT(3);
+    k_wsum_partial<T><<<g2, 256, 0, stream>>>(reinterpret_cast<const T *>(h->d_mu), d_rho_bar, h->N_d, K,
+                                              h->d_msum_part);
+    int *d_bad = reinterpret_cast<int *>(h->d_small) + 1;
+    k_msum_final<<<1, 256, 0, stream>>>(h->d_msum_part, kSumBlocks, K, R, d_bad);
+    k_adj_scalars<<<1, 32, 0, stream>>>(h->d_coef, coefd, h->d_msum, R, K, 1.0 / h->dV, U_bar, alpha, beta, diag);
+    SQ_CUDA(cudaGetLastError());
+    SQ_CUDA(cudaMemsetAsync(d_vbar, 0, sizeof(double) * h->N_d, stream));
+
+    RecursionArgs<T> a;
+    fill_args<T>(h, K, 0, a);
+    a.adj_rho_bar = d_rho_bar;
+    a.adj_alpha = alpha;
+    a.adj_beta = beta;
+    a.adj_vbar = d_vbar;
+    a.adj_kc = kc;
+    a.adj_inv_tau = 1.0 / h->tau;
+    const int nsegs = (K + kc - 1) / kc;
+    const long long stride = (long long)(2 + 2 * nsegs + kc + 1 + 3) * h->nc3;
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+    const size_t smem = recursion_smem_bytes<T>(h->natom, h->nc, 0);
+    if (smem > (size_t)dev_smem) { cudaFree(d_aux); return fail(SQ_ERR_UNSUPPORTED, "too many atoms for shared memory"); }
+    long long grid = 2LL * h->num_sms;
+    if (grid > h->N_d) grid = h->N_d;
+    if ((s = ensure(&h->d_scratch, &h->scratch_cap, sizeof(T) * (size_t)stride * grid))) { cudaFree(d_aux); return s; }
+    a.scratch = reinterpret_cast<T *>(h->d_scratch);
+    SQ_COUNT(1);
+    cudaError_t e = launch_adjoint<T>(a, h->p, stride, (int)grid, smem, stream);
+    if (e != cudaSuccess) { cudaFree(d_aux); return fail(SQ_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(e)); }
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    cudaFree(d_aux);
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_density_vjp(sq_handle h, const double *d_rho_bar, double U_bar, int checkpoint_k,
+                                    double *d_veff_bar, void *stream_)
+{
+    g_last_error[0] = 0;
+    if (!h || !d_rho_bar || !d_veff_bar) return fail(SQ_ERR_ARG, "null argument");
+    if (!h->have_density) return fail(SQ_ERR_STATE, "sq_density_vjp before sq_density");
+    if (checkpoint_k < 1 || checkpoint_k > h->K) return fail(SQ_ERR_ARG, "checkpoint interval %d (K = %d)", checkpoint_k, h->K);
+    if (!std::isfinite(U_bar)) return fail(SQ_ERR_NOT_FINITE, "U_bar");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    return h->precision == SQ_FP64 ? density_vjp<double>(h, d_rho_bar, U_bar, checkpoint_k, d_veff_bar, stream)
+                                   : density_vjp<float>(h, d_rho_bar, U_bar, checkpoint_k, d_veff_bar, stream);
+}

@@ -46,7 +46,19 @@ struct RecursionArgs {
     // vector storage
     T *scratch;          // [gridDim][2][nc3] when the vectors live in global memory
     int vec_in_smem;
+    // reverse-mode pass (adjoint_kernel only): mubar_k = adj_alpha[k] adj_rho_bar[q] + adj_beta[k]
+    const double *adj_rho_bar;
+    const double *adj_alpha;
+    const double *adj_beta;
+    double *adj_vbar;    // accumulated with atomics
+    int adj_kc;          // checkpoint interval
+    double adj_inv_tau;
 };
+
+// Vector-Jacobian pass over all columns (scratch_stride elements of per-CTA scratch).
+template <typename T>
+cudaError_t launch_adjoint(const RecursionArgs<T> &args, int fd_half, long long scratch_stride, int grid,
+                           size_t smem, cudaStream_t stream);
 
 // One work item of a batched launch: columns [begin, end) of cell `cell`.
 struct BatchItem {

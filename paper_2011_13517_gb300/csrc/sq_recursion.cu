@@ -73,9 +73,98 @@ __device__ int block_compact(bool flag, int *scan, int *total)
     return slot;
 }
 
+
+// Reverse-mode derivative of the moments of one column with respect to the diagonal of Hhat_q
+// (i.e. V_eff / tau on the cube), for the cotangent mubar_k = alpha_k rhobar_q + beta_k:
+//   a_K = mubar_K e_q,  a_k = 2 Hhat a_{k+1} - a_{k+2} + mubar_k e_q   (reverse Clenshaw),
+//   Dbar = sum_{k>=1} 2 a_{k+1} (.) v_k + a_1 (.) v_0,   Vbar(x) += Dbar(x) / tau.
+// The forward vectors are kept as checkpoint pairs (v_j, v_{j+1}) every kc steps and recomputed
+// segment by segment during the backward sweep.  vA/vB hold v_0 = e_q and v_{-1} = 0 on entry;
+// work points to the CTA's remaining scratch: [2 nseg + kc + 1 + 3] vectors.
+template <typename T, typename Dots, typename Update>
+__device__ __forceinline__ void adjoint_column(const RecursionArgs<T> &args, long long q, int centre, Dots &dots,
+                                               Update &update, T *vA, T *vB, T *work)
+{
+    const int nc3 = args.nc3, K = args.K, kc = args.adj_kc;
+    const int nsegs = (K + kc - 1) / kc;
+    T *ck = work;                                   // [2 nsegs][nc3]
+    T *seg = ck + (size_t)2 * nsegs * nc3;          // [kc + 1][nc3]
+    T *X = seg + (size_t)(kc + 1) * nc3;            // a_{k+1}
+    T *Z = X + nc3;                                 // a_{k+2}
+    T *Db = Z + nc3;                                // diagonal cotangent
+    const double rb = args.adj_rho_bar[q];
+    auto mubar = [&](int k) { return (T)(args.adj_alpha[k] * rb + args.adj_beta[k]); };
+    auto copy = [&](const T *src, T *dst) {
+        for (int i = threadIdx.x; i < nc3; i += blockDim.x) dst[i] = src[i];
+    };
+    // forward pass, storing (v_j, v_{j+1}) at j = 0, kc, 2kc, ...
+    T *vc = vA, *vp = vB;
+    for (int k = 0; k < K; k++) {
+        if (k % kc == 0) copy(vc, ck + (size_t)(2 * (k / kc)) * nc3);
+        dots(vc, k, true);
+        __syncthreads();
+        update(vc, vp, vp, k == 0 ? T(1) : T(2), k == 0 ? T(0) : T(1));
+        __syncthreads();
+        T *sw = vp;
+        vp = vc;
+        vc = sw;
+        if (k % kc == 0) copy(vc, ck + (size_t)(2 * (k / kc) + 1) * nc3);
+    }
+    // seeds: a_{K+1} = 0, a_K = mubar_K e_q
+    for (int i = threadIdx.x; i < nc3; i += blockDim.x) {
+        X[i] = (i == centre) ? mubar(K) : T(0);
+        Z[i] = T(0);
+        Db[i] = T(0);
+    }
+    __syncthreads();
+    for (int s = nsegs - 1; s >= 0; s--) {
+        const int j = s * kc;
+        const int jend = min(j + kc - 1, K - 1);
+        copy(ck + (size_t)(2 * s) * nc3, seg);
+        if (jend > j) copy(ck + (size_t)(2 * s + 1) * nc3, seg + nc3);
+        __syncthreads();
+        for (int i = 1; j + i < jend; i++) {       // seg[i+1] = v_{j+i+1}
+            dots(seg + (size_t)i * nc3, 0, true);
+            __syncthreads();
+            update(seg + (size_t)i * nc3, seg + (size_t)(i - 1) * nc3, seg + (size_t)(i + 1) * nc3, T(2), T(1));
+            __syncthreads();
+        }
+        for (int k = jend; k >= j; k--) {
+            const T wk = k >= 1 ? T(2) : T(1);
+            const T *vk = seg + (size_t)(k - j) * nc3;
+            for (int i = threadIdx.x; i < nc3; i += blockDim.x) Db[i] += wk * X[i] * vk[i];
+            if (k >= 1) {
+                dots(X, 0, true);
+                __syncthreads();
+                update(X, Z, Z, T(2), T(1));
+                __syncthreads();
+                if (threadIdx.x == 0) Z[centre] += mubar(k);
+                __syncthreads();
+                T *sw = X;
+                X = Z;
+                Z = sw;
+            }
+            __syncthreads();
+        }
+    }
+    // scatter Dbar / tau onto the global grid
+    const int q1 = (int)(q % args.n[0]);
+    const int q2 = (int)((q / args.n[0]) % args.n[1]);
+    const int q3 = (int)(q / ((long long)args.n[0] * args.n[1]));
+    for (int i = threadIdx.x; i < nc3; i += blockDim.x) {
+        const int a = i % args.nc[0], b = (i / args.nc[0]) % args.nc[1], c = i / (args.nc[0] * args.nc[1]);
+        const int g0 = pmod(q1 - args.m[0] + a, args.n[0]);
+        const int g1 = pmod(q2 - args.m[1] + b, args.n[1]);
+        const int g2 = pmod(q3 - args.m[2] + c, args.n[2]);
+        const double v = (double)Db[i] * args.adj_inv_tau;
+        if (v != 0.0) atomicAdd(args.adj_vbar + (g0 + (long long)args.n[0] * (g1 + (long long)args.n[1] * g2)), v);
+    }
+    __syncthreads();
+}
+
 // Columns q_begin, q_begin + q_step, ... < q_end of one cell, processed by the calling CTA.
 // smem_raw is the CTA's dynamic shared memory; scratch its two cube vectors when !VSMEM.
-template <typename T, int P, int BLOCK, bool VSMEM>
+template <typename T, int P, int BLOCK, bool VSMEM, bool ADJ = false>
 __device__ __forceinline__ void column_range(const RecursionArgs<T> &args, long long q_begin, long long q_end,
                                              long long q_step, unsigned char *smem_raw, T *scratch)
 {
@@ -227,13 +316,13 @@ __device__ __forceinline__ void column_range(const RecursionArgs<T> &args, long 
         const size_t dbase = (size_t)q3 * plane_p + (size_t)q2 * args.pn[0] + q1;
         const int two_nx = 2 * args.n[0], two_ny = 2 * args.n[1], two_nz = 2 * args.n[2];
 
-        for (int k = 0; k <= args.K; k++) {
-            // ---- phase 1: projector contractions of v_k -----------------------------------
-            const bool need_dots = k < args.K;
-            if (need_dots || args.want_force) {
+        const bool wforce = ADJ ? false : (bool)args.want_force;
+        // phase 1: projector contractions chi^T X (and, at step k, force moments of X)
+        auto dots = [&](const T *X, int k, bool need_dots) {
+            if (need_dots || wforce) {
                 for (int t = warp; t < nact; t += nwarp) {
                     const AtomRec r = act[t];
-                    const bool frc = args.want_force && r.fidx >= 0;
+                    const bool frc = wforce && r.fidx >= 0;
                     if (!need_dots && !frc) continue;
                     const T *fx = args.fac + r.base[0];
                     const T *fy = args.fac + r.base[1];
@@ -247,7 +336,7 @@ __device__ __forceinline__ void column_range(const RecursionArgs<T> &args, long 
                     for (int row = lane; row < nrows; row += 32) {
                         const int b = r.lo[1] + row % nry;
                         const int c = r.lo[2] + row / nry;
-                        const T *vr = vcur + (c * ncy + b) * ncx;
+                        const T *vr = X + (c * ncy + b) * ncx;
                         T Gs = 0, Hs = 0, Gd = 0, Hd = 0;
                         for (int a = r.lo[0]; a <= r.hi[0]; a++) {
                             const T val = vr[a];
@@ -319,12 +408,9 @@ __device__ __forceinline__ void column_range(const RecursionArgs<T> &args, long 
                     }
                 }
             }
-            if (k == args.K) break;
-            __syncthreads();
-
-            // ---- phase 2: w = ca Hhat v_k - cb v_{k-1}, written over v_{k-1} -------------------
-            const T ca = k == 0 ? T(1) : T(2);
-            const T cb = k == 0 ? T(0) : T(1);
+        };
+        // phase 2: O = ca Hhat X - cb Z (O may alias Z), KB term from the dots of X
+        auto update = [&](const T *X, const T *Z, T *O, T ca, T cb) {
             for (int sg = threadIdx.x; sg < nseg; sg += BLOCK) {
                 const int sx = sg % nsx;
                 const int rest = sg / nsx;
@@ -336,7 +422,7 @@ __device__ __forceinline__ void column_range(const RecursionArgs<T> &args, long 
 #pragma unroll
                 for (int i = 0; i < kSeg + 2 * P; i++) {
                     const int a = a0 - P + i;
-                    cen[i] = (a >= 0 && a < ncx) ? vcur[rowbase + a] : T(0);
+                    cen[i] = (a >= 0 && a < ncx) ? X[rowbase + a] : T(0);
                 }
                 T acc[kSeg];
                 const T *drow = args.dpad + dbase + (size_t)c * plane_p + (size_t)b * args.pn[0];
@@ -350,14 +436,14 @@ __device__ __forceinline__ void column_range(const RecursionArgs<T> &args, long 
                         for (int j = 1; j <= P; j++) sum += args.w[0][j - 1] * (cen[P + s + j] + cen[P + s - j]);
 #pragma unroll
                         for (int j = 1; j <= P; j++) {
-                            const T yp = (b + j < ncy) ? vcur[rowbase + a + j * ncx] : T(0);
-                            const T ym = (b - j >= 0) ? vcur[rowbase + a - j * ncx] : T(0);
+                            const T yp = (b + j < ncy) ? X[rowbase + a + j * ncx] : T(0);
+                            const T ym = (b - j >= 0) ? X[rowbase + a - j * ncx] : T(0);
                             sum += args.w[1][j - 1] * (yp + ym);
                         }
 #pragma unroll
                         for (int j = 1; j <= P; j++) {
-                            const T zp = (c + j < ncz) ? vcur[rowbase + a + j * ncx * ncy] : T(0);
-                            const T zm = (c - j >= 0) ? vcur[rowbase + a - j * ncx * ncy] : T(0);
+                            const T zp = (c + j < ncz) ? X[rowbase + a + j * ncx * ncy] : T(0);
+                            const T zm = (c - j >= 0) ? X[rowbase + a - j * ncx * ncy] : T(0);
                             sum += args.w[2][j - 1] * (zp + zm);
                         }
                     }
@@ -398,15 +484,25 @@ __device__ __forceinline__ void column_range(const RecursionArgs<T> &args, long 
                     const int a = a0 + s;
                     if (a < ncx) {
                         const int idx = rowbase + a;
-                        vprev[idx] = ca * acc[s] - cb * vprev[idx];
+                        O[idx] = ca * acc[s] - cb * Z[idx];
                     }
                 }
             }
-            __syncthreads();
-            T *sw = vprev;
-            vprev = vcur;
-            vcur = sw;
-            if (threadIdx.x == 0) args.mu[(size_t)(k + 1) * N_d + q] = vcur[centre];
+        };
+        if constexpr (!ADJ) {
+            for (int k = 0; k <= args.K; k++) {
+                dots(vcur, k, k < args.K);
+                if (k == args.K) break;
+                __syncthreads();
+                update(vcur, vprev, vprev, k == 0 ? T(1) : T(2), k == 0 ? T(0) : T(1));
+                __syncthreads();
+                T *sw = vprev;
+                vprev = vcur;
+                vcur = sw;
+                if (threadIdx.x == 0) args.mu[(size_t)(k + 1) * N_d + q] = vcur[centre];
+            }
+        } else {
+            adjoint_column<T>(args, q, centre, dots, update, va, vb, scratch + 2 * (size_t)nc3);
         }
         __syncthreads();
     }
@@ -418,6 +514,16 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 2 : 1) recursion_kernel(
     extern __shared__ __align__(16) unsigned char smem_raw[];
     column_range<T, P, BLOCK, VSMEM>(args, blockIdx.x, args.N_d, gridDim.x, smem_raw,
                                      VSMEM ? nullptr : args.scratch + (size_t)blockIdx.x * 2 * args.nc3);
+}
+
+// Reverse-mode (vector-Jacobian) pass over all columns: vectors in per-CTA global scratch of
+// 2 + 2 nseg + kc + 1 + 3 cube vectors.
+template <typename T, int P>
+__global__ void __launch_bounds__(256, 2) adjoint_kernel(const RecursionArgs<T> args, long long scratch_stride)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    column_range<T, P, 256, false, true>(args, blockIdx.x, args.N_d, gridDim.x, smem_raw,
+                                         args.scratch + (size_t)blockIdx.x * scratch_stride);
 }
 
 // Many cells in one persistent launch: each CTA takes (cell, column range) work items from a queue
@@ -560,6 +666,27 @@ int recursion_blocks_per_sm(int fd_half, int block, size_t smem, int vec_in_smem
     SQ_DISPATCH_P(blocks_p, block, smem, vec_in_smem)
     return 0;
 }
+
+template <typename T, int P>
+cudaError_t launch_adjoint_p(const RecursionArgs<T> &args, long long stride, int grid, size_t smem, cudaStream_t stream)
+{
+    auto kern = adjoint_kernel<T, P>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 256, smem, stream>>>(args, stride);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adjoint(const RecursionArgs<T> &args, int fd_half, long long stride, int grid, size_t smem,
+                           cudaStream_t stream)
+{
+    SQ_DISPATCH_P(launch_adjoint_p, args, stride, grid, smem, stream)
+    return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_adjoint<double>(const RecursionArgs<double> &, int, long long, int, size_t, cudaStream_t);
+template cudaError_t launch_adjoint<float>(const RecursionArgs<float> &, int, long long, int, size_t, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_batch(const BatchLaunch<T> &b, int fd_half, cudaStream_t stream)

@@ -1,0 +1,159 @@
+"""Derivatives of the SQ path with respect to V_eff.
+
+CPU: the oracle's forward-mode tangent (differentiated Chebyshev recursion plus the implicit Fermi
+level term) against central finite differences of the oracle itself.
+GPU: the reverse-mode product (sq_density_vjp, reverse Clenshaw with checkpoints) against that
+tangent through the dot-product identity <rho_bar, d rho> + U_bar dU = <V_bar, dV>, against
+pointwise tangents, across checkpoint intervals, through the torch.autograd.Function, and at the
+full size of the 95-atom vacancy cell (K = 60)."""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2011_13517_gb300 import cells
+
+
+def smooth_field(cell, seed):
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(*[np.arange(cell.n[a]) / cell.n[a] for a in (2, 1, 0)], indexing="ij")
+    f = np.zeros(cell.n[::-1])
+    for _ in range(6):
+        k = rng.integers(-2, 3, size=3)
+        f += rng.standard_normal() * np.cos(2 * np.pi * (k[0] * x + k[1] * y + k[2] * z) + rng.uniform(0, 6.28))
+    return f.reshape(-1)
+
+
+def test_oracle_tangent_matches_finite_differences():
+    """d rho, dU, d lambda_f of the oracle's tangent = central differences of the oracle's solve
+    (same fixed spectral bounds), step 1e-4 Ha along a smooth field."""
+    c = cells.tiny_cell()
+    bounds = oracle.spectral_bounds(c)
+    dV = smooth_field(c, 1)
+    drho, dU, dlam, _ = oracle.sq_tangent(c, dV, bounds=bounds)
+    eps = 1e-4
+    cp, cm = cells.tiny_cell(), cells.tiny_cell()
+    cp.veff = c.veff + eps * dV.reshape(c.veff.shape)
+    cm.veff = c.veff - eps * dV.reshape(c.veff.shape)
+    rp = oracle.sq_solve(cp, force=False, bounds=bounds)
+    rm = oracle.sq_solve(cm, force=False, bounds=bounds)
+    fd_rho = (rp["rho"] - rm["rho"]) / (2 * eps)
+    np.testing.assert_allclose(drho, fd_rho, rtol=0, atol=1e-6 * np.max(np.abs(fd_rho)))
+    assert abs(dU - (rp["U"] - rm["U"]) / (2 * eps)) < 1e-6 * max(1.0, abs(dU))
+    assert abs(dlam - (rp["lam_f"] - rm["lam_f"]) / (2 * eps)) < 1e-6 * max(1.0, abs(dlam))
+
+
+# ---------------------------------------------------------------------------------------------
+gpu = pytest.mark.gpu
+
+
+def _torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def gpu_vjp(cell, bounds, rho_bar, U_bar, kc, precision=None):
+    torch = _torch()
+    from paper_2011_13517_gb300 import sq
+    precision = sq.SQ_FP64 if precision is None else precision
+    h = sq.build_for_cell(cell, bounds=bounds)
+    rho = torch.empty(cell.N_d, dtype=torch.float64, device="cuda")
+    sq.sq_density(h, cell.K, cell.kT, cell.N_e, precision, 0, rho)
+    rb = torch.from_numpy(np.ascontiguousarray(rho_bar, dtype=np.float64)).cuda()
+    vbar = torch.empty(cell.N_d, dtype=torch.float64, device="cuda")
+    sq.sq_density_vjp(h, rb, U_bar, kc, vbar)
+    out = vbar.cpu().numpy()
+    h.close()
+    return out
+
+
+@gpu
+def test_vjp_dot_product_against_oracle_tangent():
+    c = cells.tiny_cell()
+    bounds = oracle.spectral_bounds(c)
+    rng = np.random.default_rng(2)
+    rho_bar = rng.standard_normal(c.N_d)
+    U_bar = 0.7
+    vbar = gpu_vjp(c, bounds, rho_bar, U_bar, 8)
+    for seed in (3, 4):
+        dV = smooth_field(c, seed)
+        drho, dU, _, _ = oracle.sq_tangent(c, dV, bounds=bounds)
+        lhs = float(np.dot(rho_bar, drho) + U_bar * dU)
+        rhs = float(np.dot(vbar, dV))
+        assert abs(lhs - rhs) < 1e-9 * max(abs(lhs), 1e-12), (lhs, rhs)
+
+
+@gpu
+def test_vjp_pointwise_and_checkpoint_independence():
+    """V_bar at seeded points against the oracle tangent along e_p; the same V_bar for checkpoint
+    intervals 1, 8 and 16 (K = 20: 20, 3 and 2 segments)."""
+    c = cells.tiny_cell()
+    bounds = oracle.spectral_bounds(c)
+    rng = np.random.default_rng(5)
+    rho_bar = rng.standard_normal(c.N_d)
+    U_bar = -0.3
+    v = {kc: gpu_vjp(c, bounds, rho_bar, U_bar, kc) for kc in (1, 8, 16)}
+    scale = np.max(np.abs(v[1]))
+    for kc in (8, 16):
+        np.testing.assert_allclose(v[kc], v[1], rtol=0, atol=1e-12 * scale)
+    for p in rng.choice(c.N_d, 4, replace=False):
+        e = np.zeros(c.N_d)
+        e[p] = 1.0
+        drho, dU, _, _ = oracle.sq_tangent(c, e, bounds=bounds)
+        ref = float(np.dot(rho_bar, drho) + U_bar * dU)
+        assert abs(v[8][p] - ref) < 1e-9 * scale, (p, v[8][p], ref)
+
+
+@gpu
+def test_autograd_function_matches_vjp():
+    torch = _torch()
+    from paper_2011_13517_gb300.autograd import sq_density_autograd
+    c = cells.tiny_cell()
+    bounds = oracle.spectral_bounds(c)
+    veff = torch.from_numpy(c.veff.reshape(-1).copy()).cuda().requires_grad_(True)
+    rho, U = sq_density_autograd(veff, c, bounds, checkpoint_k=4)
+    rng = np.random.default_rng(7)
+    w = torch.from_numpy(rng.standard_normal(c.N_d)).cuda()
+    loss = (w * rho).sum() + 0.5 * U
+    (g,) = torch.autograd.grad(loss, veff)
+    ref = gpu_vjp(c, bounds, w.cpu().numpy(), 0.5, 4)
+    np.testing.assert_allclose(g.cpu().numpy(), ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+    # directional check against the oracle tangent
+    dV = smooth_field(c, 8)
+    drho, dU, _, _ = oracle.sq_tangent(c, dV, bounds=bounds)
+    lhs = float(np.dot(w.cpu().numpy(), drho) + 0.5 * dU)
+    assert abs(lhs - float(np.dot(g.cpu().numpy(), dV))) < 1e-9 * abs(lhs)
+
+
+@gpu
+def test_vjp_vacancy_cell_full_size():
+    """The 95-atom vacancy cell with K = 60 (the differentiation workload): FP32 reverse mode with
+    checkpoint intervals 1, 8 and 16 agree, and the FP64 reverse-mode directional derivative along a
+    smooth field matches central differences of the FP64 forward path (step 1e-4 Ha)."""
+    torch = _torch()
+    from paper_2011_13517_gb300 import sq
+    c = cells.vacancy_cell()
+    bounds = oracle.spectral_bounds(c)
+    rng = np.random.default_rng(9)
+    rho_bar = rng.standard_normal(c.N_d)
+    U_bar = 0.25
+    v32 = {kc: gpu_vjp(c, bounds, rho_bar, U_bar, kc, precision=sq.SQ_FP32) for kc in (1, 8, 16)}
+    scale = np.max(np.abs(v32[8]))
+    for kc in (1, 16):
+        np.testing.assert_allclose(v32[kc], v32[8], rtol=0, atol=1e-6 * scale)
+    dV = smooth_field(c, 10)
+    eps = 1e-4
+    vals = []
+    for sgn in (1, -1):
+        cc = cells.vacancy_cell()
+        cc.veff = c.veff + sgn * eps * dV.reshape(c.veff.shape)
+        r = sq.solve_cell(cc, sq.SQ_FP64, force=False, bounds=bounds)
+        vals.append(float(np.dot(rho_bar, r["rho"]) + U_bar * r["U"]))
+    fd = (vals[0] - vals[1]) / (2 * eps)
+    v64 = gpu_vjp(c, bounds, rho_bar, U_bar, 8, precision=sq.SQ_FP64)
+    ad64 = float(np.dot(v64, dV))
+    ad32 = float(np.dot(v32[8], dV))
+    print("vacancy VJP directional derivative: FD", fd, "FP64", ad64, "FP32", ad32)
+    assert abs(ad64 - fd) < 1e-6 * abs(fd)
+    assert abs(ad32 - fd) < 1e-3 * abs(fd)
