@@ -187,6 +187,87 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, sq, torch, world, rank, barrier, dist):
+    """32 independent defect cells (48-288 sites, 0-2 vacancies, 0-2 Al, R_cut 5/6/7, K 40/60/80) in
+    one batch: one persistent recursion launch, autotuned, captured in a CUDA graph and replayed."""
+    precision = sq.SQ_FP64 if args.precision == "fp64" else sq.SQ_FP32
+    cs = cells.batch_cells(32)
+    handles = [sq.build_for_cell(c) for c in cs]
+    b = sq.sq_batch_create(handles, [c.K for c in cs], [c.kT for c in cs], [c.N_e for c in cs], precision, 0)
+    rhos = [torch.empty(c.N_d, dtype=torch.float64, device="cuda") for c in cs]
+    t0 = time.perf_counter()
+    sq.sq_batch_density(b, rhos)            # autotune + capture + first replay
+    first = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        sq.sq_batch_density(b, rhos)
+    stream = torch.cuda.current_stream()
+    times = []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sq.sq_batch_density(b, rhos)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    pts = sum(c.N_d for c in cs)
+    info = sq.sq_batch_info(b)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": world * pts / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision else "f64",
+                          "data": "synthetic",
+                          "config": {"workload": "batch of 32 seeded hcp defect cells (48-288 sites, 0-2 vacancies, "
+                                                 "0-2 Al, R_cut 5/6/7 bohr, K 40/60/80), one persistent launch, "
+                                                 "CUDA graph", "grid_points": pts, "first_call_s": first,
+                                     "autotuned": info},
+                          "clocks": clk.summary()}), flush=True)
+    b.close()
+
+
+def run_adjoint(args, sq, torch, world, rank, barrier, dist):
+    """Reverse-mode derivative of (rho, U) wrt V_eff on the vacancy cell (K = 60, checkpoint every 8
+    steps): one forward sq_density plus one sq_density_vjp per step."""
+    from oracle import oracle  # spectral bounds held fixed for the derivative (host-side set-up)
+    precision = sq.SQ_FP64 if args.precision == "fp64" else sq.SQ_FP32
+    c = cells.vacancy_cell()
+    bounds = oracle.spectral_bounds(c)
+    d_veff = torch.from_numpy(np.ascontiguousarray(c.veff.reshape(-1))).cuda()
+    rho = torch.empty(c.N_d, dtype=torch.float64, device="cuda")
+    rbar = torch.from_numpy(np.random.default_rng(9).standard_normal(c.N_d)).cuda()
+    vbar = torch.empty_like(rho)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h = sq.build_for_cell(c, bounds=bounds, d_veff=d_veff)
+        sq.sq_density(h, c.K, c.kT, c.N_e, precision, 0, rho)
+        sq.sq_density_vjp(h, rbar, 0.25, 8, vbar)
+        h.close()
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    if rank == 0:
+        print(json.dumps({"metric": "SQ forward + vector-Jacobian product grid-points/sec", "value": world * c.N_d / (ms * 1e-3),
+                          "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f32" if precision else "f64", "data": "synthetic",
+                          "config": dict(workload_config(c), checkpoint_k=8)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -196,6 +277,11 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="both")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed steps of the secondary FP64 measurement (0: same as --steps)")
+    ap.add_argument("--workload", choices=["vacancy", "batch", "adjoint"], default="vacancy",
+                    help="vacancy: the headline line; batch: 32 defect cells in one graph-captured batch; "
+                         "adjoint: the reverse-mode derivative of the vacancy cell")
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu: one sq_density of the same cell with K=8, no timing loop")
     args = ap.parse_args()
@@ -220,6 +306,12 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    if args.workload == "batch":
+        run_batch(args, sq, torch, world, rank, barrier, dist)
+        return
+    if args.workload == "adjoint":
+        run_adjoint(args, sq, torch, world, rank, barrier, dist)
+        return
     cell = cells.vacancy_cell()
     if args.profile:
         cell.K = 8
@@ -235,8 +327,9 @@ def main():
         U, S, F = sq.sq_energy(h)
         sq.sq_nonlocal_force(h, force)
         timing = sq.sq_get_timing(h)
+        kname = sq.sq_kernel_name(h)
         h.close()
-        return lam, U, S, timing
+        return lam, U, S, timing, kname
 
     def measure(precision, steps, warmup):
         for _ in range(warmup):
@@ -305,14 +398,16 @@ def main():
     precs = ["fp32", "fp64"] if args.precision == "both" else [args.precision]
     for p in precs:
         code = sq.SQ_FP32 if p == "fp32" else sq.SQ_FP64
-        ms, rec_ms, clocks, launches, res = measure(code, args.steps, args.warmup)
+        # the FP64 recursion runs at the GB300's FP64 rate (~33 s per step here): a single timed step
+        steps = args.steps if (p == precs[0] or args.fp64_steps <= 0) else args.fp64_steps
+        ms, rec_ms, clocks, launches, res = measure(code, steps, args.warmup)
         peak = FP32_PEAK_TFLOPS if p == "fp32" else FP64_PEAK_TFLOPS
         achieved = flops / (rec_ms * 1e-3) / 1e12
-        results[p] = dict(ms=ms, rec_ms=rec_ms, clocks=clocks, launches=launches, lam_f=res[0], U=res[1],
+        results[p] = dict(ms=ms, rec_ms=rec_ms, clocks=clocks, launches=launches, lam_f=res[0], U=res[1], steps=steps,
                           S=res[2], value=world * cell.N_d / (ms * 1e-3),
                           roofline={"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                     "frac": achieved / peak, "traffic": None,
-                                    "kernel": f"recursion_kernel<{'float' if p == 'fp32' else 'double'},6>",
+                                    "kernel": res[4],
                                     "algorithmic_tflop_per_launch": flops / 1e12,
                                     "kernel_ms": rec_ms,
                                     "peak_source": ("FP32 unit count: 152 SM x 128 lanes x 2 x 2.07 GHz"
@@ -332,7 +427,8 @@ def main():
     }
     for p in precs[1:]:
         r = results[p]
-        line[p] = {"value": r["value"], "ms_per_step": r["ms"], "roofline": r["roofline"], "clocks": r["clocks"],
+        line[p] = {"value": r["value"], "ms_per_step": r["ms"], "steps": r["steps"], "warmup": args.warmup,
+                   "roofline": r["roofline"], "clocks": r["clocks"],
                    "gpu_launches": r["launches"], "results": {"lambda_f": r["lam_f"], "U": r["U"], "S": r["S"]}}
     if "fp32" in results and "fp64" in results:
         line["fp32_vs_fp64"] = {"dlambda_f": abs(results["fp32"]["lam_f"] - results["fp64"]["lam_f"]),

@@ -188,6 +188,9 @@ sq_status sq_get_cube(sq_handle h, int m[3]);
  */
 sq_status sq_get_timing(sq_handle h, double *recursion_ms, double *msum_ms, double *fermi_ms);
 
+/* Name of the recursion kernel the last sq_density ran (static string; "" before the first call). */
+const char *sq_kernel_name(sq_handle h);
+
 /* Total number of kernels this library has launched in this process (for launch accounting). */
 long long sq_kernel_launches(void);
 

@@ -1054,6 +1054,13 @@ extern "C" sq_status sq_get_timing(sq_handle h, double *recursion_ms, double *ms
     return SQ_OK;
 }
 
+extern "C" const char *sq_kernel_name(sq_handle h)
+{
+    if (!h || !h->have_density) return "";
+    if (h->kernel_used == 1) return h->nc[0] == 21 ? "slab_kernel<21,6>" : "slab_kernel<25,6>";
+    return h->precision == SQ_FP64 ? "recursion_kernel<double>" : "recursion_kernel<float>";
+}
+
 extern "C" sq_status sq_get_cube(sq_handle h, int m[3])
 {
     if (!h || !m) return fail(SQ_ERR_ARG, "null argument");

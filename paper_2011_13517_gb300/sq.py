@@ -27,7 +27,8 @@ STATUS = {0: "SQ_OK", 1: "SQ_ERR_ARG", 2: "SQ_ERR_CUBE_EXCEEDS_BOX", 3: "SQ_ERR_
 EXPORTS = ["sq_build_hamiltonian", "sq_density", "sq_fermi_level", "sq_energy", "sq_nonlocal_force",
            "sq_get_spectral_bounds", "sq_get_moments", "sq_copy_moments", "sq_get_cube", "sq_get_timing",
            "sq_kernel_launches", "sq_moments_noalloc", "sq_batch_create", "sq_batch_density", "sq_batch_info",
-           "sq_batch_destroy", "sq_density_vjp", "sq_destroy", "sq_status_string", "sq_last_error"]
+           "sq_batch_destroy", "sq_density_vjp", "sq_kernel_name", "sq_destroy", "sq_status_string",
+           "sq_last_error"]
 
 
 class SQError(RuntimeError):
@@ -77,6 +78,8 @@ def lib():
         L.sq_batch_info.argtypes = [vp, ip, ip, ip, dp, ctypes.POINTER(ctypes.c_longlong)]
         L.sq_batch_destroy.argtypes = [vp]
         L.sq_density_vjp.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, vp, vp]
+        L.sq_kernel_name.argtypes = [vp]
+        L.sq_kernel_name.restype = ctypes.c_char_p
         L.sq_batch_destroy.restype = None
         L.sq_destroy.argtypes = [vp]
         L.sq_destroy.restype = None
@@ -84,7 +87,8 @@ def lib():
         L.sq_status_string.restype = ctypes.c_char_p
         L.sq_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("sq_destroy", "sq_status_string", "sq_last_error", "sq_kernel_launches", "sq_batch_destroy"):
+            if name not in ("sq_destroy", "sq_status_string", "sq_last_error", "sq_kernel_launches", "sq_batch_destroy",
+                            "sq_kernel_name"):
                 getattr(L, name).restype = ctypes.c_int
         L.sq_kernel_launches.restype = ctypes.c_longlong
         _lib = L
@@ -195,6 +199,10 @@ def sq_density_vjp(h: Handle, d_rho_bar, U_bar, checkpoint_k, d_veff_bar, stream
     """sq_density_vjp: d_veff_bar = dL/dV_eff for L = sum rho_bar rho + U_bar U (see include/sq.h)."""
     _check(lib().sq_density_vjp(h.ptr, _dev_ptr(d_rho_bar), float(U_bar), int(checkpoint_k), _dev_ptr(d_veff_bar),
                                 _stream(stream)))
+
+
+def sq_kernel_name(h: Handle) -> str:
+    return lib().sq_kernel_name(h.ptr).decode()
 
 
 def sq_kernel_launches() -> int:
