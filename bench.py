@@ -389,9 +389,9 @@ def main():
 
     if args.profile:
         for p in (["fp32", "fp64"] if args.precision == "both" else [args.precision]):
-            lam, U, S, timing = step(sq.SQ_FP32 if p == "fp32" else sq.SQ_FP64)
+            lam, U, S, timing, kname = step(sq.SQ_FP32 if p == "fp32" else sq.SQ_FP64)
             torch.cuda.synchronize()
-            print(json.dumps({"profile_case": p, "K": cell.K, "recursion_ms": timing[0], "lambda_f": lam}))
+            print(json.dumps({"profile_case": p, "K": cell.K, "kernel": kname, "recursion_ms": timing[0], "lambda_f": lam}))
         return
     flops = algorithmic_flops(cell)
     results = {}

@@ -1,22 +1,26 @@
-// FP32 per-column Chebyshev recursion for cubic truncation cubes of 17..32 points per axis: the
-// "slab" kernel.
+// FP32 per-column Chebyshev recursion for cubic truncation cubes of 21 or 25 points per axis with the
+// 12th-order stencil: the "slab" kernel.
 //
 // Same mathematics as recursion_kernel (Eq. Chebyshev on the truncated scaled Hamiltonian, with the
 // Kleinman-Bylander term and the force moments of Eq. NLforceSQ), mapped for the FP32 pipes:
-//   - one CTA per column, NC warps: warp b owns the y-slab b of the cube, lane a its x position;
-//     each lane keeps its z-pencil v(a, b, 0..NC-1) in registers for the whole step;
-//   - stencil: z neighbours from the lane's own registers, x neighbours by warp shuffles, y
-//     neighbours from the shared-memory copy of v_k (one conflict-free wavefront per load);
-//   - KB term: for every atom whose support covers slab b, the y factor is folded into two
-//     per-lane scalars, and the z factors come from shared-memory tables read as broadcasts;
-//   - projector contractions chi^T v: per-lane z sums, a warp reduction over x, per-warp slots in
-//     shared memory, then a fixed-order sum over the slabs (deterministic).
+//   - one CTA per column, NC warps: warp b owns the y-slab b of the cube; lane l holds the x position
+//     a = l - 6 (lanes 0..5 and those past the cube hold zeros), and its z-pencil v(a, b, 0..NC-1)
+//     stays in registers for the whole step;
+//   - stencil: z neighbours from registers, x neighbours by warp shuffles (the zero lanes on both
+//     sides make the cube boundary free of selects), y neighbours from the shared-memory copy of v_k;
+//   - KB term: for every atom whose support covers slab b, the y factor folds into two per-lane
+//     scalars; each 128-bit broadcast of the z-factor table then feeds 4 FMAs;
+//   - projector contractions chi^T v: per-lane z sums, a transposed butterfly reduction of the
+//     x-weighted sums, per-slab slots in shared memory, then a fixed-order sum over slabs
+//     (deterministic).
 #include <cuda_runtime.h>
 
 #include "sq_internal.h"
 
 namespace sq {
 namespace {
+
+constexpr int kOff = 6;   // lane of x position 0
 
 struct SlabRec {
     int J;          // atom index
@@ -29,13 +33,6 @@ __device__ __forceinline__ int smod(int a, int n)
 {
     int r = a % n;
     return r < 0 ? r + n : r;
-}
-
-__device__ __forceinline__ float wsum(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 // Support range of atom J's projector inside the cube window [wstart, wstart + nc) on one axis,
@@ -57,18 +54,68 @@ __device__ __forceinline__ bool window_range(int st, int len, int na, int nca, i
     return true;
 }
 
+// Transposed butterfly: on entry every lane holds v[0..7]; on exit the lane holds the warp-wide sum
+// of v[idx] with idx = 4 bit4(lane) + 2 bit3(lane) + bit2(lane) (9 shuffles instead of 40).
+__device__ __forceinline__ float reduce8(const float v[8], int lane)
+{
+    float a[4], b[2];
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const float send = h16 ? v[i] : v[i + 4];
+        const float keep = h16 ? v[i + 4] : v[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float send = h8 ? a[i] : a[i + 2];
+        const float keep = h8 ? a[i + 2] : a[i];
+        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float c = (h4 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h4 ? b[0] : b[1], 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
+template <int NC>
+struct Geo {
+    static constexpr int NW = NC;                  // warps: one per y-slab
+    static constexpr int NZ = (NC + 1) & ~1;       // z-table entries per atom (even: 128-bit pairs)
+};
+
+// Transposed butterfly for four values: the lane ends with the warp-wide sum of v[2 bit4 + bit3].
+__device__ __forceinline__ float reduce4(const float v[4], int lane)
+{
+    float a[2];
+    const bool h16 = lane & 16, h8 = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float send = h16 ? v[i] : v[i + 2];
+        const float keep = h16 ? v[i + 2] : v[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float c = (h8 ? a[1] : a[0]) + __shfl_xor_sync(0xffffffffu, h8 ? a[0] : a[1], 8);
+    c += __shfl_xor_sync(0xffffffffu, c, 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
 struct SlabSmem {
     float *va, *vb;
-    float2 *tab;     // [amax][3][NC] (g, hp) window tables
-    float2 *ftab;    // [fmax][3][NC] (g', hp') window tables of force atoms
-    float *slot;     // [NC][amax][4]
-    float *fslot;    // [NC][fmax][12]
-    float *sd;       // [amax][4]
-    SlabRec *rec;    // [amax]
-    double *chiq;    // [fmax][4]
-    int *ftl;        // [fmax] force slot -> active index
-    unsigned *ymask; // [NC][W]
-    int *scan;       // [40]
+    float2 *tx, *ty;   // [amax][NC] (g, hp) window tables along x and y
+    float4 *tz;        // [amax][NZ/2] (g[c], hp[c], g[c+1], hp[c+1]) along z
+    float2 *fx, *fy;   // [fmax][NC] (g', hp') of force atoms along x and y
+    float4 *fz;        // [fmax][NZ/2] (g', hp') pairs along z
+    float *slot;       // [NC][amax][4]
+    float *fslot;      // [NC][fmax][12]
+    float *sd;         // [amax][4]
+    SlabRec *rec;      // [amax]
+    double *chiq;      // [fmax][4]
+    int *ftl;          // [fmax] force slot -> active index
+    unsigned *ymask;   // [NC][W]
+    int *scan;         // [40]
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -77,26 +124,31 @@ template <int NC>
 __host__ __device__ inline size_t slab_layout(unsigned char *base, int amax, int fmax, SlabSmem *s)
 {
     const int W = (amax + 31) / 32;
+    constexpr int NZ = Geo<NC>::NZ;
     size_t off = 0;
     auto take = [&](size_t bytes) {
-        size_t o = off;
+        const size_t o = off;
         off = align16(off + bytes);
         return base ? base + o : nullptr;
     };
     const size_t nc3 = (size_t)NC * NC * NC;
     unsigned char *p;
-    p = take(sizeof(float) * nc3);                        if (s) s->va = (float *)p;
-    p = take(sizeof(float) * nc3);                        if (s) s->vb = (float *)p;
-    p = take(sizeof(float2) * (size_t)amax * 3 * NC);     if (s) s->tab = (float2 *)p;
-    p = take(sizeof(float2) * (size_t)fmax * 3 * NC);     if (s) s->ftab = (float2 *)p;
-    p = take(sizeof(float) * (size_t)NC * amax * 4);      if (s) s->slot = (float *)p;
-    p = take(sizeof(float) * (size_t)NC * fmax * 12);     if (s) s->fslot = (float *)p;
-    p = take(sizeof(float) * (size_t)amax * 4);           if (s) s->sd = (float *)p;
-    p = take(sizeof(SlabRec) * (size_t)amax);             if (s) s->rec = (SlabRec *)p;
-    p = take(sizeof(double) * (size_t)fmax * 4);          if (s) s->chiq = (double *)p;
-    p = take(sizeof(int) * (size_t)fmax);                 if (s) s->ftl = (int *)p;
-    p = take(sizeof(unsigned) * (size_t)NC * W);          if (s) s->ymask = (unsigned *)p;
-    p = take(sizeof(int) * 40);                           if (s) s->scan = (int *)p;
+    p = take(sizeof(float) * nc3);                      if (s) s->va = (float *)p;
+    p = take(sizeof(float) * nc3);                      if (s) s->vb = (float *)p;
+    p = take(sizeof(float2) * (size_t)amax * NC);       if (s) s->tx = (float2 *)p;
+    p = take(sizeof(float2) * (size_t)amax * NC);       if (s) s->ty = (float2 *)p;
+    p = take(sizeof(float2) * (size_t)amax * NZ);       if (s) s->tz = (float4 *)p;
+    p = take(sizeof(float2) * (size_t)fmax * NC);       if (s) s->fx = (float2 *)p;
+    p = take(sizeof(float2) * (size_t)fmax * NC);       if (s) s->fy = (float2 *)p;
+    p = take(sizeof(float2) * (size_t)fmax * NZ);       if (s) s->fz = (float4 *)p;
+    p = take(sizeof(float) * (size_t)NC * amax * 4);    if (s) s->slot = (float *)p;
+    p = take(sizeof(float) * (size_t)NC * fmax * 12);   if (s) s->fslot = (float *)p;
+    p = take(sizeof(float) * (size_t)amax * 4);         if (s) s->sd = (float *)p;
+    p = take(sizeof(SlabRec) * (size_t)amax);           if (s) s->rec = (SlabRec *)p;
+    p = take(sizeof(double) * (size_t)fmax * 4);        if (s) s->chiq = (double *)p;
+    p = take(sizeof(int) * (size_t)fmax);               if (s) s->ftl = (int *)p;
+    p = take(sizeof(unsigned) * (size_t)NC * W);        if (s) s->ymask = (unsigned *)p;
+    p = take(sizeof(int) * 40);                         if (s) s->scan = (int *)p;
     return off;
 }
 
@@ -147,24 +199,41 @@ __global__ void k_slab_counts(const RecursionArgs<float> args, int *counts)
     }
 }
 
+__device__ __forceinline__ float wsum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <int NC, int P>
 __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<float> args, int amax, int fmax,
                                                           int *err)
 {
+    constexpr int NZ = Geo<NC>::NZ, NTH = NC * 32;
+    static_assert(kOff >= P && kOff + NC <= 31, "lane layout: zero lanes below x = 0 and at lane 31");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SlabSmem S;
     slab_layout<NC>(smem_raw, amax, fmax, &S);
     const int W = (amax + 31) / 32;
     const int lane = threadIdx.x & 31;
-    const int b = threadIdx.x >> 5;          // slab (y index)
-    const bool live = lane < NC;             // lane holds a cube point
+    const int b = threadIdx.x >> 5;             // slab (y index)
+    const int a = lane - kOff;                  // x position
+    const bool live = a >= 0 && a < NC;
+    const int ac = live ? a : 0;
     const int m = (NC - 1) / 2;
     const int natom = args.natom;
     const int nproj = args.nproj;
     const long long N_d = args.N_d;
     const size_t plane_p = (size_t)args.pn[0] * args.pn[1];
     const float kap0 = args.kappa[0], kap1 = args.kappa[1];
-    const int two_n[3] = {2 * args.n[0], 2 * args.n[1], 2 * args.n[2]};
+    // y rows b + j that exist in the cube (warp-uniform)
+    unsigned yvalid = 0u;
+#pragma unroll
+    for (int j = 1; j <= P; j++) {
+        if (b + j < NC) yvalid |= 1u << (2 * j - 2);
+        if (b - j >= 0) yvalid |= 1u << (2 * j - 1);
+    }
 
     for (long long q = blockIdx.x; q < N_d; q += gridDim.x) {
         const int qa[3] = {(int)(q % args.n[0]), (int)((q / args.n[0]) % args.n[1]),
@@ -172,10 +241,9 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
         int wstart[3];
 #pragma unroll
         for (int ax = 0; ax < 3; ax++) wstart[ax] = smod(qa[ax] - args.m[ax], args.n[ax]);
-
         // ---- active atoms (ordered) ----
         int nact = 0;
-        for (int base = 0; base < natom; base += NC * 32) {
+        for (int base = 0; base < natom; base += NTH) {
             const int J = base + (int)threadIdx.x;
             bool on = J < natom;
             short lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -202,15 +270,27 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
         }
         __syncthreads();
         // ---- window tables ----
-        for (int it = threadIdx.x; it < nact * 3 * NC; it += NC * 32) {
-            const int o = it % NC, ax = (it / NC) % 3, t = it / (3 * NC);
-            const float *f = args.fac + (size_t)S.rec[t].J * args.fac_stride + args.fac_off[ax] + wstart[ax] + o;
-            S.tab[it] = make_float2(f[0], f[two_n[ax]]);
+        for (int it = threadIdx.x; it < nact * NC; it += NTH) {
+            const int o = it % NC, t = it / NC;
+            const float *base = args.fac + (size_t)S.rec[t].J * args.fac_stride;
+            const float *f0 = base + args.fac_off[0] + wstart[0] + o;
+            const float *f1 = base + args.fac_off[1] + wstart[1] + o;
+            S.tx[it] = make_float2(f0[0], f0[2 * args.n[0]]);
+            S.ty[it] = make_float2(f1[0], f1[2 * args.n[1]]);
+        }
+        for (int it = threadIdx.x; it < nact * NZ; it += NTH) {
+            const int o = it % NZ, t = it / NZ;
+            float2 v = make_float2(0.f, 0.f);
+            if (o < NC) {
+                const float *f2 = args.fac + (size_t)S.rec[t].J * args.fac_stride + args.fac_off[2] + wstart[2] + o;
+                v = make_float2(f2[0], f2[2 * args.n[2]]);
+            }
+            reinterpret_cast<float2 *>(S.tz)[it] = v;
         }
         // ---- force atoms: projectors nonzero at x_q ----
         int nfrc = 0;
         if (args.want_force) {
-            for (int base = 0; base < nact; base += NC * 32) {
+            for (int base = 0; base < nact; base += NTH) {
                 const int t = base + (int)threadIdx.x;
                 bool on = false;
                 const double *f = nullptr;
@@ -240,15 +320,27 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
                 continue;
             }
             __syncthreads();
-            for (int it = threadIdx.x; it < nfrc * 3 * NC; it += NC * 32) {
-                const int o = it % NC, ax = (it / NC) % 3, fi = it / (3 * NC);
-                const float *f = args.fac + (size_t)S.rec[S.ftl[fi]].J * args.fac_stride + args.fac_off[ax] +
-                                 wstart[ax] + o;
-                S.ftab[it] = make_float2(f[2 * two_n[ax]], f[3 * two_n[ax]]);
+            for (int it = threadIdx.x; it < nfrc * NC; it += NTH) {
+                const int o = it % NC, fi = it / NC;
+                const float *base = args.fac + (size_t)S.rec[S.ftl[fi]].J * args.fac_stride;
+                const float *f0 = base + args.fac_off[0] + wstart[0] + o;
+                const float *f1 = base + args.fac_off[1] + wstart[1] + o;
+                S.fx[it] = make_float2(f0[4 * args.n[0]], f0[6 * args.n[0]]);
+                S.fy[it] = make_float2(f1[4 * args.n[1]], f1[6 * args.n[1]]);
+            }
+            for (int it = threadIdx.x; it < nfrc * NZ; it += NTH) {
+                const int o = it % NZ, fi = it / NZ;
+                float2 v = make_float2(0.f, 0.f);
+                if (o < NC) {
+                    const float *f2 = args.fac + (size_t)S.rec[S.ftl[fi]].J * args.fac_stride + args.fac_off[2] +
+                                      wstart[2] + o;
+                    v = make_float2(f2[4 * args.n[2]], f2[6 * args.n[2]]);
+                }
+                reinterpret_cast<float2 *>(S.fz)[it] = v;
             }
         }
         // ---- slab coverage masks ----
-        for (int it = threadIdx.x; it < NC * W; it += NC * 32) {
+        for (int it = threadIdx.x; it < NC * W; it += NTH) {
             const int wd = it % W, bb = it / W;
             unsigned msk = 0u;
             for (int t = 32 * wd; t < min(nact, 32 * wd + 32); t++)
@@ -259,16 +351,16 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
         float vz[NC];
 #pragma unroll
         for (int c = 0; c < NC; c++) {
-            vz[c] = (live && lane == m && b == m && c == m) ? 1.0f : 0.0f;
+            vz[c] = (live && a == m && b == m && c == m) ? 1.0f : 0.0f;
             if (live) {
-                S.va[(c * NC + b) * NC + lane] = vz[c];
-                S.vb[(c * NC + b) * NC + lane] = 0.0f;
+                S.va[(c * NC + b) * NC + a] = vz[c];
+                S.vb[(c * NC + b) * NC + a] = 0.0f;
             }
         }
         if (threadIdx.x == 0) args.mu[q] = 1.0f;
         __syncthreads();
         float *vcur = S.va, *vprev = S.vb;
-        const float *drow = args.dpad + (size_t)qa[2] * plane_p + (size_t)(qa[1] + b) * args.pn[0] + qa[0] + lane;
+        const float *drow = args.dpad + (size_t)qa[2] * plane_p + (size_t)(qa[1] + b) * args.pn[0] + qa[0] + ac;
 
         for (int k = 0; k <= args.K; k++) {
             // ---- projector contractions of v_k (registers) -> per-slab slots ----
@@ -282,57 +374,75 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
                         const SlabRec r = S.rec[t];
                         const bool frc = args.want_force && r.fidx >= 0;
                         if (!need_dots && !frc) continue;
-                        const float2 *tz = S.tab + (t * 3 + 2) * NC;
-                        const float2 *fz = frc ? S.ftab + (r.fidx * 3 + 2) * NC : tz;
+                        const float4 *tz = S.tz + t * (NZ / 2);
+                        const float4 *fz = S.fz + (frc ? r.fidx : 0) * (NZ / 2);
                         float G = 0.f, H = 0.f, Gd = 0.f, Hd = 0.f;
 #pragma unroll
                         for (int c0 = 0; c0 < NC; c0 += 4) {
                             if (c0 + 3 < r.lo[2] || c0 > r.hi[2]) continue;
 #pragma unroll
-                            for (int cc = 0; cc < 4; cc++) {
-                                const int c = c0 + cc;
+                            for (int pp = 0; pp < 2; pp++) {
+                                const int c = c0 + 2 * pp;
                                 if (c < NC) {
-                                    const float2 z = tz[c];
+                                    const float4 z = tz[c >> 1];
                                     G += z.x * vz[c];
                                     H += z.y * vz[c];
+                                    if (c + 1 < NC) {
+                                        G += z.z * vz[c + 1];
+                                        H += z.w * vz[c + 1];
+                                    }
                                     if (frc) {
-                                        const float2 zd = fz[c];
+                                        const float4 zd = fz[c >> 1];
                                         Gd += zd.x * vz[c];
                                         Hd += zd.y * vz[c];
+                                        if (c + 1 < NC) {
+                                            Gd += zd.z * vz[c + 1];
+                                            Hd += zd.w * vz[c + 1];
+                                        }
                                     }
                                 }
                             }
                         }
-                        const float2 xv = live ? S.tab[(t * 3 + 0) * NC + lane] : make_float2(0.f, 0.f);
-                        const float u1 = wsum(xv.x * G), u2 = wsum(xv.y * G), u3 = wsum(xv.x * H);
-                        const float2 yv = S.tab[(t * 3 + 1) * NC + b];
-                        if (lane == 0) {
-                            float *sl = S.slot + ((size_t)b * amax + t) * 4;
-                            sl[0] = yv.x * u1;
-                            sl[1] = yv.x * u2;
-                            sl[2] = yv.y * u1;
-                            sl[3] = yv.x * u3;
-                        }
-                        if (frc) {
-                            const float2 xd = live ? S.ftab[(r.fidx * 3 + 0) * NC + lane] : make_float2(0.f, 0.f);
-                            const float v1 = wsum(xd.x * G), v3 = wsum(xv.x * Gd), v4 = wsum(xd.y * G);
-                            const float v6 = wsum(xv.y * Gd), v7 = wsum(xd.x * H), v9 = wsum(xv.x * Hd);
-                            const float2 yd = S.ftab[(r.fidx * 3 + 1) * NC + b];
-                            if (lane == 0) {
-                                float *fs = S.fslot + ((size_t)b * fmax + r.fidx) * 12;
-                                fs[0] = yv.x * v1;   // s,  d/dx
-                                fs[1] = yd.x * u1;   // s,  d/dy
-                                fs[2] = yv.x * v3;   // s,  d/dz
-                                fs[3] = yv.x * v4;   // px, d/dx
-                                fs[4] = yd.x * u2;   // px, d/dy
-                                fs[5] = yv.x * v6;   // px, d/dz
-                                fs[6] = yv.y * v1;   // py, d/dx
-                                fs[7] = yd.y * u1;   // py, d/dy
-                                fs[8] = yv.y * v3;   // py, d/dz
-                                fs[9] = yv.x * v7;   // pz, d/dx
-                                fs[10] = yd.x * u3;  // pz, d/dy
-                                fs[11] = yv.x * v9;  // pz, d/dz
+                        const float2 xv = live ? S.tx[t * NC + a] : make_float2(0.f, 0.f);
+                        const float2 yv = S.ty[t * NC + b];
+                        float *sl = S.slot + ((size_t)b * amax + t) * 4;
+                        if (!frc) {
+                            const float v4[4] = {xv.x * G, xv.y * G, xv.x * H, 0.f};
+                            const float red = reduce4(v4, lane);
+                            const int idx = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+                            if ((lane & 7) == 0) {
+                                if (idx == 0) {
+                                    sl[0] = yv.x * red;     // s
+                                    sl[2] = yv.y * red;     // p_y
+                                } else if (idx == 1) {
+                                    sl[1] = yv.x * red;     // p_x
+                                } else if (idx == 2) {
+                                    sl[3] = yv.x * red;     // p_z
+                                }
                             }
+                        } else {
+                            const float2 xd = live ? S.fx[r.fidx * NC + a] : make_float2(0.f, 0.f);
+                            const float2 yd = S.fy[r.fidx * NC + b];
+                            const float v8[8] = {xv.x * G, xv.y * G, xv.x * H, xd.x * G,
+                                                 xv.x * Gd, xd.y * G, xv.y * Gd, xd.x * H};
+                            const float red = reduce8(v8, lane);
+                            const float v9 = wsum(xv.x * Hd);
+                            const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                            float *fs = S.fslot + ((size_t)b * fmax + r.fidx) * 12;
+                            if ((lane & 3) == 0) {
+                                switch (idx) {
+                                case 0: sl[0] = yv.x * red; sl[2] = yv.y * red;      // gx G: s, p_y
+                                        fs[1] = yd.x * red; fs[7] = yd.y * red; break; //  s d/dy, py d/dy
+                                case 1: sl[1] = yv.x * red; fs[4] = yd.x * red; break; // hx G: p_x; px d/dy
+                                case 2: sl[3] = yv.x * red; fs[10] = yd.x * red; break; // gx H: p_z; pz d/dy
+                                case 3: fs[0] = yv.x * red; fs[6] = yv.y * red; break;  // g'x G: s, py d/dx
+                                case 4: fs[2] = yv.x * red; fs[8] = yv.y * red; break;  // gx Gd: s, py d/dz
+                                case 5: fs[3] = yv.x * red; break;                      // h'x G: px d/dx
+                                case 6: fs[5] = yv.x * red; break;                      // hx Gd: px d/dz
+                                default: fs[9] = yv.x * red; break;                     // g'x H: pz d/dx
+                                }
+                            }
+                            if (lane == 0) fs[11] = yv.x * v9;                          // gx Hd: pz d/dz
                         }
                     }
                 }
@@ -340,7 +450,7 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
             __syncthreads();
             // fixed-order sum of the slab slots: dots of v_k, and force moments A_k
             if (need_dots) {
-                for (int it = threadIdx.x; it < nact * 4; it += NC * 32) {
+                for (int it = threadIdx.x; it < nact * 4; it += NTH) {
                     const int t = it >> 2, comp = it & 3;
                     float s = 0.f;
                     for (int bb = 0; bb < NC; bb++)
@@ -350,7 +460,7 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
             }
             if (args.want_force) {
                 const int nf = nproj > 1 ? 12 : 3;
-                for (int it = threadIdx.x; it < nfrc * nf; it += NC * 32) {
+                for (int it = threadIdx.x; it < nfrc * nf; it += NTH) {
                     const int fi = it / nf, i = it % nf;
                     const int t = S.ftl[fi];
                     double s = 0.0;
@@ -375,25 +485,26 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
                     const int t = 32 * wd + __ffs(msk) - 1;
                     msk &= msk - 1u;
                     const float4 s = *reinterpret_cast<const float4 *>(S.sd + 4 * t);
-                    const float2 yv = S.tab[(t * 3 + 1) * NC + b];
-                    const float2 xv = live ? S.tab[(t * 3 + 0) * NC + lane] : make_float2(0.f, 0.f);
-                    // kappa_l chi (chi^T v) summed over s, p_x, p_y, p_z with the y factor folded in
+                    const float2 yv = S.ty[t * NC + b];
+                    const float2 xv = live ? S.tx[t * NC + a] : make_float2(0.f, 0.f);
+                    // kappa_l chi (chi^T v) over s, p_x, p_y, p_z with the y factor folded in
                     const float Pv = kap0 * s.x * yv.x + kap1 * s.z * yv.y;
                     const float Qv = kap1 * s.w * yv.x;
                     const float Rv = kap1 * s.y * yv.x;
                     const float A1 = xv.x * Pv + xv.y * Rv;
                     const float A2 = xv.x * Qv;
                     const short lo = S.rec[t].lo[2], hi = S.rec[t].hi[2];
-                    const float2 *tz = S.tab + (t * 3 + 2) * NC;
+                    const float4 *tz = S.tz + t * (NZ / 2);
 #pragma unroll
                     for (int c0 = 0; c0 < NC; c0 += 4) {
                         if (c0 + 3 < lo || c0 > hi) continue;
 #pragma unroll
-                        for (int cc = 0; cc < 4; cc++) {
-                            const int c = c0 + cc;
+                        for (int pp = 0; pp < 2; pp++) {
+                            const int c = c0 + 2 * pp;
                             if (c < NC) {
-                                const float2 z = tz[c];
+                                const float4 z = tz[c >> 1];
                                 w[c] += z.x * A1 + z.y * A2;
+                                if (c + 1 < NC) w[c + 1] += z.z * A1 + z.w * A2;
                             }
                         }
                     }
@@ -404,7 +515,7 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
 #pragma unroll
             for (int c = 0; c < NC; c++) {
                 const float x = vz[c];
-                float t = live ? drow[(size_t)c * plane_p] * x : 0.f;
+                float t = 0.f;
 #pragma unroll
                 for (int j = 1; j <= P; j++) {
                     const float zp = (c + j < NC) ? vz[c + j] : 0.f;
@@ -413,29 +524,27 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
                 }
 #pragma unroll
                 for (int j = 1; j <= P; j++) {
-                    float xp = __shfl_down_sync(0xffffffffu, x, j);
-                    float xm = __shfl_up_sync(0xffffffffu, x, j);
-                    xp = (lane + j < NC) ? xp : 0.f;
-                    xm = (lane >= j) ? xm : 0.f;
+                    const float xp = __shfl_sync(0xffffffffu, x, min(lane + j, 31));
+                    const float xm = __shfl_sync(0xffffffffu, x, lane - j);
                     t += args.w[0][j - 1] * (xp + xm);
                 }
                 if (live) {
-                    const float *row = vcur + (size_t)(c * NC + b) * NC + lane;
+                    const float *row = vcur + (size_t)(c * NC + b) * NC + a;
 #pragma unroll
                     for (int j = 1; j <= P; j++) {
-                        const float yp = (b + j < NC) ? row[j * NC] : 0.f;
-                        const float ym = (b - j >= 0) ? row[-j * NC] : 0.f;
+                        const float yp = (yvalid >> (2 * j - 2)) & 1u ? row[j * NC] : 0.f;
+                        const float ym = (yvalid >> (2 * j - 1)) & 1u ? row[-j * NC] : 0.f;
                         t += args.w[1][j - 1] * (yp + ym);
                     }
-                    float *pv = vprev + (size_t)(c * NC + b) * NC + lane;
-                    const float nv = ca * (w[c] + t) - cb * (*pv);
+                    float *pv = vprev + (size_t)(c * NC + b) * NC + a;
+                    const float nv = ca * (w[c] + t + drow[(size_t)c * plane_p] * x) - cb * (*pv);
                     *pv = nv;
                     w[c] = nv;
                 } else {
                     w[c] = 0.f;
                 }
             }
-            if (live && lane == m && b == m) args.mu[(size_t)(k + 1) * N_d + q] = w[m];
+            if (live && a == m && b == m) args.mu[(size_t)(k + 1) * N_d + q] = w[m];
             __syncthreads();
             float *sw = vprev;
             vprev = vcur;
@@ -454,7 +563,7 @@ cudaError_t launch_nc(const RecursionArgs<float> &args, int amax, int fmax, int 
     auto kern = slab_kernel<NC, P>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, NC * 32, smem, stream>>>(args, amax, fmax, err);
+    kern<<<grid, Geo<NC>::NW * 32, smem, stream>>>(args, amax, fmax, err);
     return cudaGetLastError();
 }
 
