@@ -49,13 +49,24 @@ def workload_config(cell):
     }
 
 
+def support_mask(R_a, L_a, n_a, rc):
+    """Grid indices of one axis inside the projector support: some periodic image of the atom lies
+    closer than the window radius rc (the window (1 - t^2/rc^2)^3 vanishes from |t| = rc on)."""
+    x = np.arange(n_a) * (L_a / n_a)
+    t = x - R_a
+    t = t - L_a * np.round(t / L_a)               # nearest image
+    inside = np.abs(t) < rc
+    for shift in (-L_a, L_a):                     # further images, for windows wider than half the box
+        inside |= np.abs(t + shift) < rc
+    return inside
+
+
 def algorithmic_flops(cell):
     """FLOPs of one recursion-kernel launch counted from the method's definition: per column and
     recursion step, the FD stencil (3 n_o + 1 FMAs per cube point) plus the Chebyshev update (1 FMA),
     plus for each projector 2 |supp chi ^ C_q| FMAs (chi^T v and the rank-1 update); force moments
     add 3 |supp ^ C_q| FMAs per projector of the atoms whose projectors are nonzero at x_q, at each of
     the K+1 vectors.  FLOPs = 2 x FMAs."""
-    from oracle import oracle  # geometry of the projector supports (host-side counting only)
     nc3 = int(np.prod(cell.n_c))
     nproj = 1 if cell.lmax == 0 else 4
     stencil = cell.K * nc3 * (3 * cell.fd_order + 2)
@@ -66,7 +77,7 @@ def algorithmic_flops(cell):
     for J in range(cell.natom):
         per_axis, per_axis_q = [], []
         for a in range(3):
-            g = oracle.axis_factors(cell.R[J, a], cell.box[a], cell.n[a], cell.proj_sigma, cell.proj_rc)[0] != 0
+            g = support_mask(cell.R[J, a], cell.box[a], int(cell.n[a]), cell.proj_rc)
             n = int(cell.n[a])
             nc = int(cell.n_c[a])
             g2 = np.concatenate([g, g]).astype(np.int64)
@@ -192,12 +203,22 @@ def run_batch(args, sq, torch, world, rank, barrier, dist):
     one batch: one persistent recursion launch, autotuned, captured in a CUDA graph and replayed."""
     precision = sq.SQ_FP64 if args.precision == "fp64" else sq.SQ_FP32
     cs = cells.batch_cells(32)
+    if args.profile:   # small case for ncu: the first four cells with K = 8
+        cs = cs[:4]
+        for c in cs:
+            c.K = 8
     handles = [sq.build_for_cell(c) for c in cs]
     b = sq.sq_batch_create(handles, [c.K for c in cs], [c.kT for c in cs], [c.N_e for c in cs], precision, 0)
     rhos = [torch.empty(c.N_d, dtype=torch.float64, device="cuda") for c in cs]
     t0 = time.perf_counter()
     sq.sq_batch_density(b, rhos)            # autotune + capture + first replay
     first = time.perf_counter() - t0
+    if args.profile:
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "batch", "cells": len(cs), "K": 8, "first_call_s": first,
+                          "autotuned": sq.sq_batch_info(b)}), flush=True)
+        b.close()
+        return
     for _ in range(args.warmup):
         sq.sq_batch_density(b, rhos)
     stream = torch.cuda.current_stream()
@@ -231,11 +252,16 @@ def run_batch(args, sq, torch, world, rank, barrier, dist):
 def run_adjoint(args, sq, torch, world, rank, barrier, dist):
     """Reverse-mode derivative of (rho, U) wrt V_eff on the vacancy cell (K = 60, checkpoint every 8
     steps): one forward sq_density plus one sq_density_vjp per step."""
-    from oracle import oracle  # spectral bounds held fixed for the derivative (host-side set-up)
     precision = sq.SQ_FP64 if args.precision == "fp64" else sq.SQ_FP32
     c = cells.vacancy_cell()
-    bounds = oracle.spectral_bounds(c)
+    kc = 8
+    if args.profile:   # small case for ncu: K = 8, checkpoint every 4 steps, one forward + VJP
+        c.K, kc = 8, 4
     d_veff = torch.from_numpy(np.ascontiguousarray(c.veff.reshape(-1))).cuda()
+    # the derivative holds the spectral bounds fixed: take the library's bounds once and pass them in
+    h0 = sq.build_for_cell(c, d_veff=d_veff)
+    bounds = sq.sq_get_spectral_bounds(h0)
+    h0.close()
     rho = torch.empty(c.N_d, dtype=torch.float64, device="cuda")
     rbar = torch.from_numpy(np.random.default_rng(9).standard_normal(c.N_d)).cuda()
     vbar = torch.empty_like(rho)
@@ -244,8 +270,14 @@ def run_adjoint(args, sq, torch, world, rank, barrier, dist):
     def step():
         h = sq.build_for_cell(c, bounds=bounds, d_veff=d_veff)
         sq.sq_density(h, c.K, c.kT, c.N_e, precision, 0, rho)
-        sq.sq_density_vjp(h, rbar, 0.25, 8, vbar)
+        sq.sq_density_vjp(h, rbar, 0.25, kc, vbar)
         h.close()
+
+    if args.profile:
+        step()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "adjoint", "K": c.K, "checkpoint_k": kc}), flush=True)
+        return
 
     for _ in range(args.warmup):
         step()
@@ -265,7 +297,7 @@ def run_adjoint(args, sq, torch, world, rank, barrier, dist):
                           "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                           "dtype": "f32" if precision else "f64", "data": "synthetic",
-                          "config": dict(workload_config(c), checkpoint_k=8)}), flush=True)
+                          "config": dict(workload_config(c), checkpoint_k=kc)}), flush=True)
 
 
 def main():
@@ -283,7 +315,8 @@ def main():
                     help="vacancy: the headline line; batch: 32 defect cells in one graph-captured batch; "
                          "adjoint: the reverse-mode derivative of the vacancy cell")
     ap.add_argument("--profile", action="store_true",
-                    help="small case for ncu: one sq_density of the same cell with K=8, no timing loop")
+                    help="small case for ncu, no timing loop: one sq_density of the same cell with K=8 "
+                         "(batch: the first four cells, K=8; adjoint: K=8, checkpoint every 4 steps)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
