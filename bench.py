@@ -434,9 +434,12 @@ def main():
         # the FP64 recursion runs at the GB300's FP64 rate (~33 s per step here): a single timed step
         steps = args.steps if (p == precs[0] or args.fp64_steps <= 0) else args.fp64_steps
         ms, rec_ms, clocks, launches, res = measure(code, steps, args.warmup)
+        torch.cuda.synchronize()
+        rho_out, force_out = rho.cpu().numpy().copy(), force.cpu().numpy().copy()   # after the timed region
         peak = FP32_PEAK_TFLOPS if p == "fp32" else FP64_PEAK_TFLOPS
         achieved = flops / (rec_ms * 1e-3) / 1e12
         results[p] = dict(ms=ms, rec_ms=rec_ms, clocks=clocks, launches=launches, lam_f=res[0], U=res[1], steps=steps,
+                          rho=rho_out, force=force_out,
                           S=res[2], value=world * cell.N_d / (ms * 1e-3),
                           roofline={"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                     "frac": achieved / peak, "traffic": None,
@@ -464,9 +467,17 @@ def main():
                    "roofline": r["roofline"], "clocks": r["clocks"],
                    "gpu_launches": r["launches"], "results": {"lambda_f": r["lam_f"], "U": r["U"], "S": r["S"]}}
     if "fp32" in results and "fp64" in results:
-        line["fp32_vs_fp64"] = {"dlambda_f": abs(results["fp32"]["lam_f"] - results["fp64"]["lam_f"]),
-                                "dU_per_atom": abs(results["fp32"]["U"] - results["fp64"]["U"]) / cell.natom,
-                                "speedup": results["fp32"]["value"] / results["fp64"]["value"]}
+        # the rho error stated with the FP32 throughput, against the FP64 path of the same run (which
+        # the parity tests hold to the FP64 oracle at 1e-10 relative)
+        r32, r64 = results["fp32"], results["fp64"]
+        drho = np.abs(r32["rho"] - r64["rho"])
+        line["fp32_vs_fp64"] = {"rho_rel_l1": float(drho.sum() * float(np.prod(cell.h)) / cell.N_e),
+                                "rho_max_rel": float((drho / np.maximum(np.abs(r64["rho"]), 1e-300)).max()),
+                                "dU_per_atom": abs(r32["U"] - r64["U"]) / cell.natom,
+                                "force_max_abs": float(np.abs(r32["force"] - r64["force"]).max()),
+                                "dlambda_f": abs(r32["lam_f"] - r64["lam_f"]),
+                                "units": "rho_rel_l1 = sum|d rho| dV / N_e; dU Ha/atom; force Ha/bohr; lambda_f Ha",
+                                "speedup": r32["value"] / r64["value"]}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cell)
     if dist is not None:

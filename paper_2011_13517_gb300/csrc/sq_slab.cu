@@ -6,13 +6,18 @@
 //   - one CTA per column, NC warps: warp b owns the y-slab b of the cube; lane l holds the x position
 //     a = l - 6 (lanes 0..5 and those past the cube hold zeros), and its z-pencil v(a, b, 0..NC-1)
 //     stays in registers for the whole step;
-//   - stencil: z neighbours from registers, x neighbours by warp shuffles (the zero lanes on both
-//     sides make the cube boundary free of selects), y neighbours from the shared-memory copy of v_k;
-//   - KB term: for every atom whose support covers slab b, the y factor folds into two per-lane
-//     scalars; each 128-bit broadcast of the z-factor table then feeds 4 FMAs;
-//   - projector contractions chi^T v: per-lane z sums, a transposed butterfly reduction of the
-//     x-weighted sums, per-slab slots in shared memory, then a fixed-order sum over slabs
-//     (deterministic).
+//   - local part first: z neighbours from registers, x neighbours by warp shuffles (the zero lanes on
+//     both sides make the cube boundary free of selects), y neighbours from the shared-memory copy of
+//     v_k; the result goes to the accumulator pencil w and the registers of v_k are free again;
+//   - KB term added into w two atoms per pass: for each atom whose support covers slab b, the y
+//     factor folds into two per-lane scalars, and each 128-bit broadcast of a z-factor table feeds 4
+//     FMAs; the z loops run over the whole zero-padded table (no range branches);
+//   - projector contractions chi^T v: per-lane z sums (two atoms per pass; atoms with force moments
+//     in a pass of their own), a transposed butterfly reduction of the x-weighted sums, per-slab slots
+//     in shared memory, then a fixed-order sum over slabs (deterministic);
+//   - two barriers per step: after the slab slots are written and after their sums are formed.  The
+//     buffer written by step k is next read, and the buffer read by step k next written, behind the
+//     two barriers of step k+1.
 #include <cuda_runtime.h>
 
 #include "sq_internal.h"
@@ -115,6 +120,8 @@ struct SlabSmem {
     double *chiq;      // [fmax][4]
     int *ftl;          // [fmax] force slot -> active index
     unsigned *ymask;   // [NC][W]
+    unsigned *fbits;   // [W] force atoms among the active ones
+    float4 *zero;      // [NZ/2] zero z-table (partner of an unpaired atom)
     int *scan;         // [40]
 };
 
@@ -148,6 +155,8 @@ __host__ __device__ inline size_t slab_layout(unsigned char *base, int amax, int
     p = take(sizeof(double) * (size_t)fmax * 4);        if (s) s->chiq = (double *)p;
     p = take(sizeof(int) * (size_t)fmax);               if (s) s->ftl = (int *)p;
     p = take(sizeof(unsigned) * (size_t)NC * W);        if (s) s->ymask = (unsigned *)p;
+    p = take(sizeof(unsigned) * (size_t)W);             if (s) s->fbits = (unsigned *)p;
+    p = take(sizeof(float4) * (size_t)(NZ / 2));        if (s) s->zero = (float4 *)p;
     p = take(sizeof(int) * 40);                         if (s) s->scan = (int *)p;
     return off;
 }
@@ -234,6 +243,8 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
         if (b + j < NC) yvalid |= 1u << (2 * j - 2);
         if (b - j >= 0) yvalid |= 1u << (2 * j - 1);
     }
+
+    for (int i = threadIdx.x; i < NZ / 2; i += NTH) S.zero[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     for (long long q = blockIdx.x; q < N_d; q += gridDim.x) {
         const int qa[3] = {(int)(q % args.n[0]), (int)((q / args.n[0]) % args.n[1]),
@@ -347,6 +358,12 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
                 if (bb >= S.rec[t].lo[1] && bb <= S.rec[t].hi[1]) msk |= 1u << (t - 32 * wd);
             S.ymask[it] = msk;
         }
+        for (int wd = threadIdx.x; wd < W; wd += NTH) {
+            unsigned fb = 0u;
+            for (int t = 32 * wd; t < min(nact, 32 * wd + 32); t++)
+                if (S.rec[t].fidx >= 0) fb |= 1u << (t - 32 * wd);
+            S.fbits[wd] = fb;
+        }
         // ---- v_0 = e_q, v_{-1} = 0 ----
         float vz[NC];
 #pragma unroll
@@ -367,83 +384,99 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
             const bool need_dots = k < args.K;
             if (need_dots || args.want_force) {
                 for (int wd = 0; wd < W; wd++) {
-                    unsigned msk = S.ymask[b * W + wd];
+                    const unsigned all = S.ymask[b * W + wd];
+                    const unsigned fb = S.fbits[wd];
+                    // atoms without force moments, two per pass
+                    unsigned msk = need_dots ? (all & ~fb) : 0u;
+                    while (msk) {
+                        const int t0 = 32 * wd + __ffs(msk) - 1;
+                        msk &= msk - 1u;
+                        const bool two = msk != 0u;
+                        const int t1 = two ? 32 * wd + __ffs(msk) - 1 : t0;
+                        msk &= msk - 1u;
+                        const float4 *z0 = S.tz + t0 * (NZ / 2);
+                        const float4 *z1 = two ? S.tz + t1 * (NZ / 2) : S.zero;
+                        float G0a = 0.f, H0a = 0.f, G0b = 0.f, H0b = 0.f;
+                        float G1a = 0.f, H1a = 0.f, G1b = 0.f, H1b = 0.f;
+#pragma unroll
+                        for (int c = 0; c < NC; c += 2) {
+                            const float4 p0 = z0[c >> 1], p1 = z1[c >> 1];
+                            G0a += p0.x * vz[c];
+                            H0a += p0.y * vz[c];
+                            G1a += p1.x * vz[c];
+                            H1a += p1.y * vz[c];
+                            if (c + 1 < NC) {
+                                G0b += p0.z * vz[c + 1];
+                                H0b += p0.w * vz[c + 1];
+                                G1b += p1.z * vz[c + 1];
+                                H1b += p1.w * vz[c + 1];
+                            }
+                        }
+                        const float G0 = G0a + G0b, H0 = H0a + H0b, G1 = G1a + G1b, H1 = H1a + H1b;
+                        const float2 x0 = live ? S.tx[t0 * NC + a] : make_float2(0.f, 0.f);
+                        const float2 x1 = live ? S.tx[t1 * NC + a] : make_float2(0.f, 0.f);
+                        // per atom: g_x G -> s, hp_x G -> p_x, g_x H -> p_z (y factor g), g_x G -> p_y (y factor hp)
+                        const float v8[8] = {x0.x * G0, x0.y * G0, x0.x * H0, x0.x * G0,
+                                             x1.x * G1, x1.y * G1, x1.x * H1, x1.x * G1};
+                        const float red = reduce8(v8, lane);
+                        const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                        if ((lane & 3) == 0 && (idx < 4 || two)) {
+                            const int t = idx < 4 ? t0 : t1;
+                            const int comp = idx & 3;
+                            const float2 yv = S.ty[t * NC + b];
+                            S.slot[((size_t)b * amax + t) * 4 + (comp == 2 ? 3 : comp == 3 ? 2 : comp)] =
+                                (comp == 3 ? yv.y : yv.x) * red;
+                        }
+                    }
+                    // atoms with force moments: projector and derivative contractions
+                    msk = args.want_force ? (all & fb) : 0u;
                     while (msk) {
                         const int t = 32 * wd + __ffs(msk) - 1;
                         msk &= msk - 1u;
-                        const SlabRec r = S.rec[t];
-                        const bool frc = args.want_force && r.fidx >= 0;
-                        if (!need_dots && !frc) continue;
+                        const int fidx = S.rec[t].fidx;
                         const float4 *tz = S.tz + t * (NZ / 2);
-                        const float4 *fz = S.fz + (frc ? r.fidx : 0) * (NZ / 2);
-                        float G = 0.f, H = 0.f, Gd = 0.f, Hd = 0.f;
+                        const float4 *fz = S.fz + fidx * (NZ / 2);
+                        float Ga = 0.f, Ha = 0.f, Gda = 0.f, Hda = 0.f, Gb = 0.f, Hb = 0.f, Gdb = 0.f, Hdb = 0.f;
 #pragma unroll
-                        for (int c0 = 0; c0 < NC; c0 += 4) {
-                            if (c0 + 3 < r.lo[2] || c0 > r.hi[2]) continue;
-#pragma unroll
-                            for (int pp = 0; pp < 2; pp++) {
-                                const int c = c0 + 2 * pp;
-                                if (c < NC) {
-                                    const float4 z = tz[c >> 1];
-                                    G += z.x * vz[c];
-                                    H += z.y * vz[c];
-                                    if (c + 1 < NC) {
-                                        G += z.z * vz[c + 1];
-                                        H += z.w * vz[c + 1];
-                                    }
-                                    if (frc) {
-                                        const float4 zd = fz[c >> 1];
-                                        Gd += zd.x * vz[c];
-                                        Hd += zd.y * vz[c];
-                                        if (c + 1 < NC) {
-                                            Gd += zd.z * vz[c + 1];
-                                            Hd += zd.w * vz[c + 1];
-                                        }
-                                    }
-                                }
+                        for (int c = 0; c < NC; c += 2) {
+                            const float4 z = tz[c >> 1], zd = fz[c >> 1];
+                            Ga += z.x * vz[c];
+                            Ha += z.y * vz[c];
+                            Gda += zd.x * vz[c];
+                            Hda += zd.y * vz[c];
+                            if (c + 1 < NC) {
+                                Gb += z.z * vz[c + 1];
+                                Hb += z.w * vz[c + 1];
+                                Gdb += zd.z * vz[c + 1];
+                                Hdb += zd.w * vz[c + 1];
                             }
                         }
+                        const float G = Ga + Gb, H = Ha + Hb, Gd = Gda + Gdb, Hd = Hda + Hdb;
                         const float2 xv = live ? S.tx[t * NC + a] : make_float2(0.f, 0.f);
                         const float2 yv = S.ty[t * NC + b];
                         float *sl = S.slot + ((size_t)b * amax + t) * 4;
-                        if (!frc) {
-                            const float v4[4] = {xv.x * G, xv.y * G, xv.x * H, 0.f};
-                            const float red = reduce4(v4, lane);
-                            const int idx = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
-                            if ((lane & 7) == 0) {
-                                if (idx == 0) {
-                                    sl[0] = yv.x * red;     // s
-                                    sl[2] = yv.y * red;     // p_y
-                                } else if (idx == 1) {
-                                    sl[1] = yv.x * red;     // p_x
-                                } else if (idx == 2) {
-                                    sl[3] = yv.x * red;     // p_z
-                                }
+                        const float2 xd = live ? S.fx[fidx * NC + a] : make_float2(0.f, 0.f);
+                        const float2 yd = S.fy[fidx * NC + b];
+                        const float v8[8] = {xv.x * G, xv.y * G, xv.x * H, xd.x * G,
+                                             xv.x * Gd, xd.y * G, xv.y * Gd, xd.x * H};
+                        const float red = reduce8(v8, lane);
+                        const float v9 = wsum(xv.x * Hd);
+                        const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                        float *fs = S.fslot + ((size_t)b * fmax + fidx) * 12;
+                        if ((lane & 3) == 0) {
+                            switch (idx) {
+                            case 0: sl[0] = yv.x * red; sl[2] = yv.y * red;      // gx G: s, p_y
+                                    fs[1] = yd.x * red; fs[7] = yd.y * red; break; //  s d/dy, py d/dy
+                            case 1: sl[1] = yv.x * red; fs[4] = yd.x * red; break; // hx G: p_x; px d/dy
+                            case 2: sl[3] = yv.x * red; fs[10] = yd.x * red; break; // gx H: p_z; pz d/dy
+                            case 3: fs[0] = yv.x * red; fs[6] = yv.y * red; break;  // g'x G: s, py d/dx
+                            case 4: fs[2] = yv.x * red; fs[8] = yv.y * red; break;  // gx Gd: s, py d/dz
+                            case 5: fs[3] = yv.x * red; break;                      // h'x G: px d/dx
+                            case 6: fs[5] = yv.x * red; break;                      // hx Gd: px d/dz
+                            default: fs[9] = yv.x * red; break;                     // g'x H: pz d/dx
                             }
-                        } else {
-                            const float2 xd = live ? S.fx[r.fidx * NC + a] : make_float2(0.f, 0.f);
-                            const float2 yd = S.fy[r.fidx * NC + b];
-                            const float v8[8] = {xv.x * G, xv.y * G, xv.x * H, xd.x * G,
-                                                 xv.x * Gd, xd.y * G, xv.y * Gd, xd.x * H};
-                            const float red = reduce8(v8, lane);
-                            const float v9 = wsum(xv.x * Hd);
-                            const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                            float *fs = S.fslot + ((size_t)b * fmax + r.fidx) * 12;
-                            if ((lane & 3) == 0) {
-                                switch (idx) {
-                                case 0: sl[0] = yv.x * red; sl[2] = yv.y * red;      // gx G: s, p_y
-                                        fs[1] = yd.x * red; fs[7] = yd.y * red; break; //  s d/dy, py d/dy
-                                case 1: sl[1] = yv.x * red; fs[4] = yd.x * red; break; // hx G: p_x; px d/dy
-                                case 2: sl[3] = yv.x * red; fs[10] = yd.x * red; break; // gx H: p_z; pz d/dy
-                                case 3: fs[0] = yv.x * red; fs[6] = yv.y * red; break;  // g'x G: s, py d/dx
-                                case 4: fs[2] = yv.x * red; fs[8] = yv.y * red; break;  // gx Gd: s, py d/dz
-                                case 5: fs[3] = yv.x * red; break;                      // h'x G: px d/dx
-                                case 6: fs[5] = yv.x * red; break;                      // hx Gd: px d/dz
-                                default: fs[9] = yv.x * red; break;                     // g'x H: pz d/dx
-                                }
-                            }
-                            if (lane == 0) fs[11] = yv.x * v9;                          // gx Hd: pz d/dz
                         }
+                        if (lane == 0) fs[11] = yv.x * v9;                          // gx Hd: pz d/dz
                     }
                 }
             }
@@ -475,43 +508,8 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
             if (k == args.K) break;
             __syncthreads();
 
-            // ---- KB term of Hhat v_k, from the dots ----
+            // ---- local part: stencil + diagonal of Hhat v_k into w (v_k's registers die here) ----
             float w[NC];
-#pragma unroll
-            for (int c = 0; c < NC; c++) w[c] = 0.f;
-            for (int wd = 0; wd < W; wd++) {
-                unsigned msk = S.ymask[b * W + wd];
-                while (msk) {
-                    const int t = 32 * wd + __ffs(msk) - 1;
-                    msk &= msk - 1u;
-                    const float4 s = *reinterpret_cast<const float4 *>(S.sd + 4 * t);
-                    const float2 yv = S.ty[t * NC + b];
-                    const float2 xv = live ? S.tx[t * NC + a] : make_float2(0.f, 0.f);
-                    // kappa_l chi (chi^T v) over s, p_x, p_y, p_z with the y factor folded in
-                    const float Pv = kap0 * s.x * yv.x + kap1 * s.z * yv.y;
-                    const float Qv = kap1 * s.w * yv.x;
-                    const float Rv = kap1 * s.y * yv.x;
-                    const float A1 = xv.x * Pv + xv.y * Rv;
-                    const float A2 = xv.x * Qv;
-                    const short lo = S.rec[t].lo[2], hi = S.rec[t].hi[2];
-                    const float4 *tz = S.tz + t * (NZ / 2);
-#pragma unroll
-                    for (int c0 = 0; c0 < NC; c0 += 4) {
-                        if (c0 + 3 < lo || c0 > hi) continue;
-#pragma unroll
-                        for (int pp = 0; pp < 2; pp++) {
-                            const int c = c0 + 2 * pp;
-                            if (c < NC) {
-                                const float4 z = tz[c >> 1];
-                                w[c] += z.x * A1 + z.y * A2;
-                                if (c + 1 < NC) w[c + 1] += z.z * A1 + z.w * A2;
-                            }
-                        }
-                    }
-                }
-            }
-            // ---- stencil + diagonal, w = ca Hhat v_k - cb v_{k-1} over v_{k-1} ----
-            const float ca = k == 0 ? 1.f : 2.f, cb = k == 0 ? 0.f : 1.f;
 #pragma unroll
             for (int c = 0; c < NC; c++) {
                 const float x = vz[c];
@@ -536,8 +534,51 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
                         const float ym = (yvalid >> (2 * j - 1)) & 1u ? row[-j * NC] : 0.f;
                         t += args.w[1][j - 1] * (yp + ym);
                     }
+                    w[c] = t + drow[(size_t)c * plane_p] * x;
+                } else {
+                    w[c] = 0.f;
+                }
+            }
+            // ---- KB term of Hhat v_k, from the dots ----
+            for (int wd = 0; wd < W; wd++) {
+                unsigned msk = S.ymask[b * W + wd];
+                while (msk) {   // two atoms per pass
+                    const int t0 = 32 * wd + __ffs(msk) - 1;
+                    msk &= msk - 1u;
+                    const bool two = msk != 0u;
+                    const int t1 = two ? 32 * wd + __ffs(msk) - 1 : t0;
+                    msk &= msk - 1u;
+                    float A1[2], A2[2];
+#pragma unroll
+                    for (int i = 0; i < 2; i++) {
+                        const int t = i ? t1 : t0;
+                        const float4 s = *reinterpret_cast<const float4 *>(S.sd + 4 * t);
+                        const float2 yv = S.ty[t * NC + b];
+                        const float2 xv = live ? S.tx[t * NC + a] : make_float2(0.f, 0.f);
+                        // kappa_l chi (chi^T v) over s, p_x, p_y, p_z with the y factor folded in
+                        const float Pv = kap0 * s.x * yv.x + kap1 * s.z * yv.y;
+                        const float Qv = kap1 * s.w * yv.x;
+                        const float Rv = kap1 * s.y * yv.x;
+                        A1[i] = xv.x * Pv + xv.y * Rv;
+                        A2[i] = xv.x * Qv;
+                    }
+                    const float4 *z0 = S.tz + t0 * (NZ / 2);
+                    const float4 *z1 = two ? S.tz + t1 * (NZ / 2) : S.zero;
+#pragma unroll
+                    for (int c = 0; c < NC; c += 2) {
+                        const float4 p0 = z0[c >> 1], p1 = z1[c >> 1];
+                        w[c] += p0.x * A1[0] + p0.y * A2[0] + p1.x * A1[1] + p1.y * A2[1];
+                        if (c + 1 < NC) w[c + 1] += p0.z * A1[0] + p0.w * A2[0] + p1.z * A1[1] + p1.w * A2[1];
+                    }
+                }
+            }
+            // ---- v_{k+1} = ca Hhat v_k - cb v_{k-1} ----
+            const float ca = k == 0 ? 1.f : 2.f, cb = k == 0 ? 0.f : 1.f;
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+                if (live) {
                     float *pv = vprev + (size_t)(c * NC + b) * NC + a;
-                    const float nv = ca * (w[c] + t + drow[(size_t)c * plane_p] * x) - cb * (*pv);
+                    const float nv = ca * w[c] - cb * (*pv);
                     *pv = nv;
                     w[c] = nv;
                 } else {
@@ -545,7 +586,8 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
                 }
             }
             if (live && a == m && b == m) args.mu[(size_t)(k + 1) * N_d + q] = w[m];
-            __syncthreads();
+            // no barrier here: the next reads of the buffer just written, and the next writes of the
+            // buffer just read, sit behind the two barriers of the next step's contraction phase
             float *sw = vprev;
             vprev = vcur;
             vcur = sw;
