@@ -1188,7 +1188,9 @@ extern "C" sq_status sq_moments_noalloc(sq_handle h, int K, int precision, void 
 }
 
 // ------------------------------------------------------------------------------------------------
-// Batched evaluation: many cells, one persistent recursion launch, a CUDA graph.
+// Batched evaluation: many cells, one persistent recursion launch, a CUDA graph.  In FP32, cells whose
+// cubes the slab kernel covers (cubic 21^3 / 25^3, 12th-order stencil) run as one slab launch each,
+// captured in the same graph after the persistent launch over the other cells.
 
 // Fermi state initialised on the device (capturable: no host memory behind the copy)
 __global__ void k_fermi_init(FermiState *st, double lo, double hi)
@@ -1240,6 +1242,10 @@ struct sq_batch_s {
     double tuned_ms = 0;
     size_t graph_nodes = 0;
     long long kernels_per_replay = 0;
+    // FP32 slab cells: atom capacities and shared memory per cell (0: the cell is in the work queue)
+    int slab_ready = 0, ngeneric = 0;
+    std::vector<int> slab_amax, slab_fmax;
+    std::vector<size_t> slab_smem;
 };
 
 template <typename T>
@@ -1375,40 +1381,44 @@ extern "C" sq_status sq_batch_create(const sq_handle *cells, int ncells, const i
 }
 
 template <typename T>
-static sq_status batch_enqueue(sq_batch b, double *const *d_rho, cudaStream_t stream, int config, int chunk,
-                               int limit_items, float *ms_out)
+static sq_status batch_enqueue(sq_batch b, const RecursionArgs<T> *host_args, double *const *d_rho,
+                               cudaStream_t stream, int config, int chunk, int limit_items, float *ms_out)
 {
     const int nc = (int)b->cells.size();
     int dev_smem = 0, num_sms = b->cells[0]->num_sms;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->cells[0]->dev);
+    // work items: column chunks of every cell outside the slab path
+    std::vector<BatchItem> items;
     int max_natom = 0, max_nc[3] = {0, 0, 0};
-    for (auto h : b->cells) {
+    for (int i = 0; i < nc; i++) {
+        if (b->slab_amax[i] != 0) continue;
+        sq_handle h = b->cells[i];
         max_natom = std::max(max_natom, h->natom);
         for (int a = 0; a < 3; a++) max_nc[a] = std::max(max_nc[a], h->nc[a]);
+        for (long long q = 0; q < h->N_d; q += chunk) items.push_back({i, 0, q, q + chunk});
     }
-    BatchLaunch<T> L;
-    memset(&L, 0, sizeof(L));
-    L.vec_in_smem = config != 2;
-    L.block = config == 0 ? 512 : 256;
-    L.smem = recursion_smem_bytes<T>(max_natom, max_nc, L.vec_in_smem);
-    if (L.smem > (size_t)dev_smem) return fail(SQ_ERR_UNSUPPORTED, "configuration %d does not fit", config);
-    const int per_sm = batch_blocks_per_sm<T>(b->fd_half, L.block, L.smem, L.vec_in_smem);
-    if (per_sm < 1) return fail(SQ_ERR_UNSUPPORTED, "configuration %d does not fit on an SM", config);
-    L.grid = per_sm * num_sms;
-    if (!L.vec_in_smem && (size_t)L.grid * b->scratch_stride * sizeof(T) > b->scratch_cap)
-        L.grid = (int)(b->scratch_cap / (b->scratch_stride * sizeof(T)));
-    // work items: column chunks of every cell
-    std::vector<BatchItem> items;
-    for (int i = 0; i < nc; i++)
-        for (long long q = 0; q < b->cells[i]->N_d; q += chunk) items.push_back({i, 0, q, q + chunk});
+    if (items.empty() && ms_out) return fail(SQ_ERR_UNSUPPORTED, "no cell in the work queue");
     int nitems = (int)items.size();
     if (limit_items > 0 && nitems > limit_items) nitems = limit_items;
-    if (!b->d_items || b->nitems < (int)items.size() || b->chunk != chunk) {
-        if (b->d_items) cudaFree(b->d_items);
-        SQ_CUDA(cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size()));
-        SQ_CUDA(cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
-        b->nitems = (int)items.size();
-        b->chunk = chunk;
+    BatchLaunch<T> L;
+    memset(&L, 0, sizeof(L));
+    if (nitems > 0) {
+        L.vec_in_smem = config != 2;
+        L.block = config == 0 ? 512 : 256;
+        L.smem = recursion_smem_bytes<T>(max_natom, max_nc, L.vec_in_smem);
+        if (L.smem > (size_t)dev_smem) return fail(SQ_ERR_UNSUPPORTED, "configuration %d does not fit", config);
+        const int per_sm = batch_blocks_per_sm<T>(b->fd_half, L.block, L.smem, L.vec_in_smem);
+        if (per_sm < 1) return fail(SQ_ERR_UNSUPPORTED, "configuration %d does not fit on an SM", config);
+        L.grid = per_sm * num_sms;
+        if (!L.vec_in_smem && (size_t)L.grid * b->scratch_stride * sizeof(T) > b->scratch_cap)
+            L.grid = (int)(b->scratch_cap / (b->scratch_stride * sizeof(T)));
+        if (!b->d_items || b->nitems < (int)items.size() || b->chunk != chunk) {
+            if (b->d_items) cudaFree(b->d_items);
+            SQ_CUDA(cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size()));
+            SQ_CUDA(cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+            b->nitems = (int)items.size();
+            b->chunk = chunk;
+        }
     }
     L.cells = reinterpret_cast<const RecursionArgs<T> *>(b->d_cells);
     L.items = b->d_items;
@@ -1440,8 +1450,10 @@ static sq_status batch_enqueue(sq_batch b, double *const *d_rho, cudaStream_t st
         SQ_CUDA(cudaEventCreate(&e1));
         SQ_CUDA(cudaEventRecord(e0, stream));
     }
-    SQ_COUNT(1);
-    SQ_CUDA(launch_batch<T>(L, b->fd_half, stream));
+    if (nitems > 0) {
+        SQ_COUNT(1);
+        SQ_CUDA(launch_batch<T>(L, b->fd_half, stream));
+    }
     if (ms_out) {
         SQ_CUDA(cudaEventRecord(e1, stream));
         SQ_CUDA(cudaEventSynchronize(e1));
@@ -1449,6 +1461,17 @@ static sq_status batch_enqueue(sq_batch b, double *const *d_rho, cudaStream_t st
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         return SQ_OK;   // timing run of the recursion only
+    }
+    if constexpr (sizeof(T) == 4) {
+        for (int i = 0; i < nc; i++) {
+            if (b->slab_amax[i] == 0) continue;
+            sq_handle h = b->cells[i];
+            int *d_err = reinterpret_cast<int *>(h->d_small) + 42;
+            SQ_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), stream));
+            SQ_COUNT(1);
+            SQ_CUDA(launch_slab(host_args[i], b->slab_amax[i], b->slab_fmax[i], (int)std::min<long long>(h->num_sms, h->N_d),
+                                b->slab_smem[i], d_err, stream));
+        }
     }
     // per-cell moment sums, Fermi level (fixed number of bisection launches), weights and density
     for (int i = 0; i < nc; i++) {
@@ -1489,6 +1512,40 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
     std::vector<RecursionArgs<T>> args(nc);
     for (int i = 0; i < nc; i++) fill_args<T>(b->cells[i], b->K[i], b->want_force && b->cells[i]->natom > 0, args[i]);
     SQ_CUDA(cudaMemcpy(b->d_cells, args.data(), sizeof(RecursionArgs<T>) * nc, cudaMemcpyHostToDevice));
+    // once: which cells take the FP32 slab kernel, with the atom capacities of their cubes
+    if (!b->slab_ready) {
+        b->slab_amax.assign(nc, 0);
+        b->slab_fmax.assign(nc, 0);
+        b->slab_smem.assign(nc, 0);
+        if constexpr (sizeof(T) == 4) {
+            int dev_smem = 0;
+            cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->cells[0]->dev);
+            for (int i = 0; i < nc; i++) {
+                sq_handle h = b->cells[i];
+                if (h->natom == 0 || !slab_supported(h->nc, h->p)) continue;
+                int *d_cnt = reinterpret_cast<int *>(h->d_small) + 40;
+                SQ_CUDA(cudaMemsetAsync(d_cnt, 0, 3 * sizeof(int), b->cap_stream));
+                SQ_COUNT(1);
+                SQ_CUDA(slab_counts(args[i], d_cnt, h->num_sms, b->cap_stream));
+                int cnt[2];
+                SQ_CUDA(cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, b->cap_stream));
+                SQ_CUDA(cudaStreamSynchronize(b->cap_stream));
+                const int amax = cnt[0] > 0 ? cnt[0] : 1, fmax = cnt[1] > 0 ? cnt[1] : 1;
+                const size_t sm = slab_smem_bytes(h->nc[0], amax, fmax);
+                if (sm > (size_t)dev_smem) continue;
+                b->slab_amax[i] = amax;
+                b->slab_fmax[i] = fmax;
+                b->slab_smem[i] = sm;
+            }
+        }
+        b->ngeneric = 0;
+        for (int i = 0; i < nc; i++) b->ngeneric += b->slab_amax[i] == 0;
+        b->slab_ready = 1;
+        if (b->ngeneric == 0) {   // no work queue: nothing to tune
+            b->config = 1;
+            b->chunk = 128;
+        }
+    }
     // autotune once: kernel configuration x work-item size, timed on a prefix of the work queue
     if (b->config < 0) {
         SQ_CUDA(cudaStreamSynchronize(stream));
@@ -1502,10 +1559,12 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
                 // each probe times the same number of columns: two per SM per work-item size, at most a
                 // sixth of the batch
                 long long total = 0;
-                for (auto h : b->cells) total += h->N_d;
+                for (int i = 0; i < nc; i++)
+                    if (b->slab_amax[i] == 0) total += b->cells[i]->N_d;
                 long long cols = std::min<long long>((long long)b->cells[0]->num_sms * 2 * 512, total / 6);
                 const int probe = (int)std::max<long long>(1, cols / chunks[ki]);
-                if (batch_enqueue<T>(b, d_rho, b->cap_stream, configs[ci], chunks[ki], probe, &ms) != SQ_OK) continue;
+                if (batch_enqueue<T>(b, args.data(), d_rho, b->cap_stream, configs[ci], chunks[ki], probe, &ms) != SQ_OK)
+                    continue;
                 if (ms < best) {
                     best = ms;
                     bc = configs[ci];
@@ -1518,7 +1577,7 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
         b->tuned_ms = best;
         b->nitems = 0;
         g_last_error[0] = 0;
-        sq_status s = batch_enqueue<T>(b, d_rho, b->cap_stream, bc, bk, 1, &best);   // build the item table
+        sq_status s = batch_enqueue<T>(b, args.data(), d_rho, b->cap_stream, bc, bk, 1, &best);   // item table
         if (s) return s;
         b->chunk = bk;
     }
@@ -1531,7 +1590,7 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
         b->graph = nullptr;
         SQ_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
         const long long before = g_launches;
-        sq_status s = batch_enqueue<T>(b, d_rho, b->cap_stream, b->config, b->chunk, 0, nullptr);
+        sq_status s = batch_enqueue<T>(b, args.data(), d_rho, b->cap_stream, b->config, b->chunk, 0, nullptr);
         b->kernels_per_replay = g_launches - before;
         g_launches = before;
         cudaGraph_t g = nullptr;
@@ -1559,6 +1618,12 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
         SQ_CUDA(cudaMemcpy(&bad, h->d_small, sizeof(int), cudaMemcpyDeviceToHost));
         SQ_CUDA(cudaMemcpy(&fin, st, sizeof(fin), cudaMemcpyDeviceToHost));
         if (bad) return fail(SQ_ERR_NOT_FINITE, "cell %d: moment sums are not finite", i);
+        h->kernel_used = b->slab_amax[i] > 0 ? 1 : 0;
+        if (h->kernel_used) {
+            int slab_err = 0;
+            SQ_CUDA(cudaMemcpy(&slab_err, reinterpret_cast<int *>(h->d_small) + 42, sizeof(int), cudaMemcpyDeviceToHost));
+            if (slab_err) return fail(SQ_ERR_UNSUPPORTED, "cell %d: a column exceeded the slab kernel's atom capacity", i);
+        }
         if (fin.phase == 4)
             return fail(SQ_ERR_NO_BRACKET, "cell %d: N(lambda_min) = %.6g, N(lambda_max) = %.6g, N_e = %.6g", i,
                         fin.N_lo, fin.N_hi, b->N_e[i]);

@@ -26,41 +26,52 @@ def small_batch():
     return out
 
 
+def _check_batch_against_single_cell(group, precision):
+    handles = [sq.build_for_cell(c) for c in group]
+    b = sq.sq_batch_create(handles, [c.K for c in group], [c.kT for c in group], [c.N_e for c in group],
+                           precision, sq.SQ_WANT_FORCE)
+    rhos = [torch.empty(c.N_d, dtype=torch.float64, device="cuda") for c in group]
+    lam = sq.sq_batch_density(b, rhos)
+    info = sq.sq_batch_info(b)
+    assert info["graph_nodes"] > 0 and info["config"] in (0, 1, 2)
+    got = []
+    for h, c, r in zip(handles, group, rhos):
+        U, S, F = sq.sq_energy(h)
+        f = torch.empty((c.natom, 3), dtype=torch.float64, device="cuda")
+        sq.sq_nonlocal_force(h, f)
+        got.append((r.cpu().numpy(), U, f.cpu().numpy()))
+    # second call replays the same graph
+    lam2 = sq.sq_batch_density(b, rhos)
+    assert np.array_equal(lam, lam2)
+    for i, (c, r) in enumerate(zip(group, rhos)):
+        assert np.array_equal(r.cpu().numpy(), got[i][0])
+        ref = sq.solve_cell(c, precision, force=True)
+        tol = 1e-12 if precision == sq.SQ_FP64 else 1e-5
+        assert abs(lam[i] - ref["lam_f"]) < tol
+        rs = np.max(np.abs(ref["rho"]))
+        np.testing.assert_allclose(got[i][0], ref["rho"], rtol=0, atol=(1e-10 if precision == sq.SQ_FP64 else 1e-4) * rs)
+        assert abs(got[i][1] - ref["U"]) < (1e-10 if precision == sq.SQ_FP64 else 1e-4) * max(1.0, abs(ref["U"]))
+        fs = max(np.max(np.abs(ref["force"])), 1e-12)
+        np.testing.assert_allclose(got[i][2], ref["force"], rtol=0,
+                                   atol=(1e-9 * fs if precision == sq.SQ_FP64 else 1e-4))
+    b.close()
+    for h in handles:
+        h.close()
+
+
 @pytest.mark.parametrize("precision", [sq.SQ_FP64, sq.SQ_FP32])
 def test_batch_matches_single_cell_path_and_replays(precision):
+    """Mixed batch: in FP32 the 21^3 and 25^3 cells take slab launches and the 29^3 cell the work
+    queue of the persistent launch, all in one graph."""
     cs = small_batch()
     # the tiny cell uses the 6th-order stencil; a batch shares one FD order, so it runs on its own
     for group in ([cs[0]], cs[1:]):
-        handles = [sq.build_for_cell(c) for c in group]
-        b = sq.sq_batch_create(handles, [c.K for c in group], [c.kT for c in group], [c.N_e for c in group],
-                               precision, sq.SQ_WANT_FORCE)
-        rhos = [torch.empty(c.N_d, dtype=torch.float64, device="cuda") for c in group]
-        lam = sq.sq_batch_density(b, rhos)
-        info = sq.sq_batch_info(b)
-        assert info["graph_nodes"] > 0 and info["config"] in (0, 1, 2)
-        got = []
-        for h, c, r in zip(handles, group, rhos):
-            U, S, F = sq.sq_energy(h)
-            f = torch.empty((c.natom, 3), dtype=torch.float64, device="cuda")
-            sq.sq_nonlocal_force(h, f)
-            got.append((r.cpu().numpy(), U, f.cpu().numpy()))
-        # second call replays the same graph
-        lam2 = sq.sq_batch_density(b, rhos)
-        assert np.array_equal(lam, lam2)
-        for i, (c, r) in enumerate(zip(group, rhos)):
-            assert np.array_equal(r.cpu().numpy(), got[i][0])
-            ref = sq.solve_cell(c, precision, force=True)
-            tol = 1e-12 if precision == sq.SQ_FP64 else 1e-5
-            assert abs(lam[i] - ref["lam_f"]) < tol
-            rs = np.max(np.abs(ref["rho"]))
-            np.testing.assert_allclose(got[i][0], ref["rho"], rtol=0, atol=(1e-10 if precision == sq.SQ_FP64 else 1e-4) * rs)
-            assert abs(got[i][1] - ref["U"]) < (1e-10 if precision == sq.SQ_FP64 else 1e-4) * max(1.0, abs(ref["U"]))
-            fs = max(np.max(np.abs(ref["force"])), 1e-12)
-            np.testing.assert_allclose(got[i][2], ref["force"], rtol=0,
-                                       atol=(1e-9 * fs if precision == sq.SQ_FP64 else 1e-4))
-        b.close()
-        for h in handles:
-            h.close()
+        _check_batch_against_single_cell(group, precision)
+
+
+def test_fp32_batch_of_slab_cells_only():
+    """FP32 batch whose every cell takes the slab kernel: no work queue, slab launches only."""
+    _check_batch_against_single_cell(small_batch()[1:3], sq.SQ_FP32)
 
 
 def test_batch_fp64_sampled_columns_match_oracle():
