@@ -200,7 +200,8 @@ def run_reference(args, rank, world):
 
 def run_batch(args, sq, torch, world, rank, barrier, dist):
     """32 independent defect cells (48-288 sites, 0-2 vacancies, 0-2 Al, R_cut 5/6/7, K 40/60/80) in
-    one batch: one persistent recursion launch, autotuned, captured in a CUDA graph and replayed."""
+    one batch: one persistent recursion launch, autotuned (in FP32 the 21^3/25^3 cells take slab
+    launches), captured in a CUDA graph and replayed.  About 4 minutes per FP32 replay."""
     precision = sq.SQ_FP64 if args.precision == "fp64" else sq.SQ_FP32
     cs = cells.batch_cells(32)
     if args.profile:   # small case for ncu: the first four cells with K = 8
@@ -242,8 +243,9 @@ def run_batch(args, sq, torch, world, rank, barrier, dist):
                           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision else "f64",
                           "data": "synthetic",
                           "config": {"workload": "batch of 32 seeded hcp defect cells (48-288 sites, 0-2 vacancies, "
-                                                 "0-2 Al, R_cut 5/6/7 bohr, K 40/60/80), one persistent launch, "
-                                                 "CUDA graph", "grid_points": pts, "first_call_s": first,
+                                                 "0-2 Al, R_cut 5/6/7 bohr, K 40/60/80), one persistent launch "
+                                                 "(FP32: 21^3/25^3 cells as slab launches), CUDA graph",
+                                     "grid_points": pts, "first_call_s": first,
                                      "autotuned": info},
                           "clocks": clk.summary()}), flush=True)
     b.close()

@@ -249,6 +249,9 @@ sq_status sq_density_vjp(sq_handle h, const double *d_rho_bar, double U_bar, int
  * Sec. 3 per cell): every cell's per-point recursion runs in ONE persistent kernel launch whose CTAs
  * take (cell, column-range) work items from a queue, followed by each cell's moment sums, Fermi
  * level, weights and density -- the whole sequence captured once into a CUDA graph and replayed.
+ * In SQ_FP32, cells with cubic 21^3 or 25^3 cubes and the 12th-order stencil leave the queue and run
+ * as one launch each of the FP32 slab kernel (the kernel sq_density uses for them), captured in the
+ * same graph.
  *
  * sq_batch_create -- group built handles (cells may differ in grid, cube, atoms, K, kT, N_e; they must
  * share the FD order and the device).  Allocates every buffer the graph will use.
@@ -263,8 +266,8 @@ sq_status sq_batch_create(const sq_handle *cells, int ncells, const int *K, cons
 
 /*
  * sq_batch_density -- run the batch.  The first call autotunes the recursion launch (vectors in shared
- * memory with 512 or 256 threads, or in global scratch; work items of 32, 128 or 512 columns), timed
- * on a prefix of the work queue, then captures the graph; later calls with the same d_rho pointers
+ * memory with 512 or 256 threads, or in global scratch; work items of 32 or 128 columns), timed on
+ * a prefix of the work queue (256 columns per SM), then captures the graph; later calls with the same d_rho pointers
  * replay it (new pointers trigger a new capture).  Afterwards each handle holds its cell's results as
  * after sq_density, so sq_energy and sq_nonlocal_force apply per cell.
  *   d_rho[ncells]   device FP64 density outputs, one per cell (caller-owned)

@@ -1550,18 +1550,18 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
     if (b->config < 0) {
         SQ_CUDA(cudaStreamSynchronize(stream));
         const int configs[3] = {0, 1, 2};
-        const int chunks[3] = {32, 128, 512};
+        const int chunks[2] = {32, 128};
         float best = 1e30f;
         int bc = -1, bk = 128;
         for (int ci = 0; ci < 3; ci++)
-            for (int ki = 0; ki < 3; ki++) {
+            for (int ki = 0; ki < 2; ki++) {
                 float ms = 0;
-                // each probe times the same number of columns: two per SM per work-item size, at most a
-                // sixth of the batch
+                // each probe times the same number of columns, 256 per SM (one 128-column item per CTA at
+                // two CTAs per SM), at most a sixth of the work queue
                 long long total = 0;
                 for (int i = 0; i < nc; i++)
                     if (b->slab_amax[i] == 0) total += b->cells[i]->N_d;
-                long long cols = std::min<long long>((long long)b->cells[0]->num_sms * 2 * 512, total / 6);
+                long long cols = std::min<long long>((long long)b->cells[0]->num_sms * 2 * 128, total / 6);
                 const int probe = (int)std::max<long long>(1, cols / chunks[ki]);
                 if (batch_enqueue<T>(b, args.data(), d_rho, b->cap_stream, configs[ci], chunks[ki], probe, &ms) != SQ_OK)
                     continue;
