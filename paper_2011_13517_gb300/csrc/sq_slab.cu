@@ -11,10 +11,13 @@
 //     v_k; the result goes to the accumulator pencil w and the registers of v_k are free again;
 //   - KB term added into w two atoms per pass: for each atom whose support covers slab b, the y
 //     factor folds into two per-lane scalars, and each 128-bit broadcast of a z-factor table feeds 4
-//     FMAs; the z loops run over the whole zero-padded table (no range branches);
-//   - projector contractions chi^T v: per-lane z sums (two atoms per pass; atoms with force moments
-//     in a pass of their own), a transposed butterfly reduction of the x-weighted sums, per-slab slots
-//     in shared memory, then a fixed-order sum over slabs (deterministic);
+//     FMAs; the z loops have no range branches: atoms whose support in the cube lies in the lower
+//     or the upper half of the z range are paired among themselves and loop over that half only,
+//     the others over the whole zero-padded table;
+//   - projector contractions chi^T v: per-lane z sums (two atoms per pass, grouped by z half as
+//     above; atoms with force moments in a pass of their own), a transposed butterfly reduction of
+//     the x-weighted sums, per-slab slots in shared memory, then a fixed-order sum over slabs
+//     (deterministic);
 //   - two barriers per step: after the slab slots are written and after their sums are formed.  The
 //     buffer written by step k is next read, and the buffer read by step k next written, behind the
 //     two barriers of step k+1.
@@ -87,6 +90,7 @@ template <int NC>
 struct Geo {
     static constexpr int NW = NC;                  // warps: one per y-slab
     static constexpr int NZ = (NC + 1) & ~1;       // z-table entries per atom (even: 128-bit pairs)
+    static constexpr int HALF = ((NC - 1) / 2) & ~1;  // even split point of the z range
 };
 
 // Transposed butterfly for four values: the lane ends with the warp-wide sum of v[2 bit4 + bit3].
@@ -121,6 +125,8 @@ struct SlabSmem {
     int *ftl;          // [fmax] force slot -> active index
     unsigned *ymask;   // [NC][W]
     unsigned *fbits;   // [W] force atoms among the active ones
+    unsigned *zlo;     // [W] atoms whose support in the cube lies in z <= NC/2 - 1/2 (lower half)
+    unsigned *zhi;     // [W] atoms whose support in the cube lies in z >= NC/2 - 1/2 (upper half)
     float4 *zero;      // [NZ/2] zero z-table (partner of an unpaired atom)
     int *scan;         // [40]
 };
@@ -156,6 +162,8 @@ __host__ __device__ inline size_t slab_layout(unsigned char *base, int amax, int
     p = take(sizeof(int) * (size_t)fmax);               if (s) s->ftl = (int *)p;
     p = take(sizeof(unsigned) * (size_t)NC * W);        if (s) s->ymask = (unsigned *)p;
     p = take(sizeof(unsigned) * (size_t)W);             if (s) s->fbits = (unsigned *)p;
+    p = take(sizeof(unsigned) * (size_t)W);             if (s) s->zlo = (unsigned *)p;
+    p = take(sizeof(unsigned) * (size_t)W);             if (s) s->zhi = (unsigned *)p;
     p = take(sizeof(float4) * (size_t)(NZ / 2));        if (s) s->zero = (float4 *)p;
     p = take(sizeof(int) * 40);                         if (s) s->scan = (int *)p;
     return off;
@@ -215,11 +223,96 @@ __device__ __forceinline__ float wsum(float v)
     return v;
 }
 
+// Projector contractions of two atoms per pass over z in [C0, C1) (C0 even; the tables are zero
+// outside each atom's support, so a range that covers the support gives the full sums).
+template <int NC, int C0, int C1>
+__device__ __forceinline__ void dots_pairs(unsigned msk, int wd, const SlabSmem &S, const float (&vz)[NC], int b,
+                                           int a, bool live, int lane, int amax)
+{
+    constexpr int NZ = Geo<NC>::NZ;
+    while (msk) {
+        const int t0 = 32 * wd + __ffs(msk) - 1;
+        msk &= msk - 1u;
+        const bool two = msk != 0u;
+        const int t1 = two ? 32 * wd + __ffs(msk) - 1 : t0;
+        msk &= msk - 1u;
+        const float4 *z0 = S.tz + t0 * (NZ / 2);
+        const float4 *z1 = two ? S.tz + t1 * (NZ / 2) : S.zero;
+        float G0a = 0.f, H0a = 0.f, G0b = 0.f, H0b = 0.f;
+        float G1a = 0.f, H1a = 0.f, G1b = 0.f, H1b = 0.f;
+#pragma unroll
+        for (int c = C0; c < C1; c += 2) {
+            const float4 p0 = z0[c >> 1], p1 = z1[c >> 1];
+            G0a += p0.x * vz[c];
+            H0a += p0.y * vz[c];
+            G1a += p1.x * vz[c];
+            H1a += p1.y * vz[c];
+            if (c + 1 < NC) {
+                G0b += p0.z * vz[c + 1];
+                H0b += p0.w * vz[c + 1];
+                G1b += p1.z * vz[c + 1];
+                H1b += p1.w * vz[c + 1];
+            }
+        }
+        const float G0 = G0a + G0b, H0 = H0a + H0b, G1 = G1a + G1b, H1 = H1a + H1b;
+        const float2 x0 = live ? S.tx[t0 * NC + a] : make_float2(0.f, 0.f);
+        const float2 x1 = live ? S.tx[t1 * NC + a] : make_float2(0.f, 0.f);
+        // per atom: g_x G -> s, hp_x G -> p_x, g_x H -> p_z (y factor g), g_x G -> p_y (y factor hp)
+        const float v8[8] = {x0.x * G0, x0.y * G0, x0.x * H0, x0.x * G0, x1.x * G1, x1.y * G1, x1.x * H1, x1.x * G1};
+        const float red = reduce8(v8, lane);
+        const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        if ((lane & 3) == 0 && (idx < 4 || two)) {
+            const int t = idx < 4 ? t0 : t1;
+            const int comp = idx & 3;
+            const float2 yv = S.ty[t * NC + b];
+            S.slot[((size_t)b * amax + t) * 4 + (comp == 2 ? 3 : comp == 3 ? 2 : comp)] = (comp == 3 ? yv.y : yv.x) * red;
+        }
+    }
+}
+
+// KB update of two atoms per pass over z in [C0, C1): w += kappa_l chi (chi^T v) from the dots.
+template <int NC, int C0, int C1>
+__device__ __forceinline__ void update_pairs(unsigned msk, int wd, const SlabSmem &S, float (&w)[NC], int b, int a,
+                                             bool live, float kap0, float kap1)
+{
+    constexpr int NZ = Geo<NC>::NZ;
+    while (msk) {
+        const int t0 = 32 * wd + __ffs(msk) - 1;
+        msk &= msk - 1u;
+        const bool two = msk != 0u;
+        const int t1 = two ? 32 * wd + __ffs(msk) - 1 : t0;
+        msk &= msk - 1u;
+        float A1[2], A2[2];
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int t = i ? t1 : t0;
+            const float4 s = *reinterpret_cast<const float4 *>(S.sd + 4 * t);
+            const float2 yv = S.ty[t * NC + b];
+            const float2 xv = live ? S.tx[t * NC + a] : make_float2(0.f, 0.f);
+            // kappa_l chi (chi^T v) over s, p_x, p_y, p_z with the y factor folded in
+            const float Pv = kap0 * s.x * yv.x + kap1 * s.z * yv.y;
+            const float Qv = kap1 * s.w * yv.x;
+            const float Rv = kap1 * s.y * yv.x;
+            A1[i] = xv.x * Pv + xv.y * Rv;
+            A2[i] = xv.x * Qv;
+        }
+        const float4 *z0 = S.tz + t0 * (NZ / 2);
+        const float4 *z1 = two ? S.tz + t1 * (NZ / 2) : S.zero;
+#pragma unroll
+        for (int c = C0; c < C1; c += 2) {
+            const float4 p0 = z0[c >> 1], p1 = z1[c >> 1];
+            w[c] += p0.x * A1[0] + p0.y * A2[0] + p1.x * A1[1] + p1.y * A2[1];
+            if (c + 1 < NC) w[c + 1] += p0.z * A1[0] + p0.w * A2[0] + p1.z * A1[1] + p1.w * A2[1];
+        }
+    }
+}
+
 template <int NC, int P>
 __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<float> args, int amax, int fmax,
                                                           int *err)
 {
     constexpr int NZ = Geo<NC>::NZ, NTH = NC * 32;
+    constexpr int kHalf = Geo<NC>::HALF;
     static_assert(kOff >= P && kOff + NC <= 31, "lane layout: zero lanes below x = 0 and at lane 31");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SlabSmem S;
@@ -359,10 +452,16 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
             S.ymask[it] = msk;
         }
         for (int wd = threadIdx.x; wd < W; wd += NTH) {
-            unsigned fb = 0u;
-            for (int t = 32 * wd; t < min(nact, 32 * wd + 32); t++)
-                if (S.rec[t].fidx >= 0) fb |= 1u << (t - 32 * wd);
+            unsigned fb = 0u, zl = 0u, zh = 0u;
+            for (int t = 32 * wd; t < min(nact, 32 * wd + 32); t++) {
+                const unsigned bit = 1u << (t - 32 * wd);
+                if (S.rec[t].fidx >= 0) fb |= bit;
+                if (S.rec[t].hi[2] <= kHalf) zl |= bit;
+                else if (S.rec[t].lo[2] >= kHalf) zh |= bit;
+            }
             S.fbits[wd] = fb;
+            S.zlo[wd] = zl;
+            S.zhi[wd] = zh;
         }
         // ---- v_0 = e_q, v_{-1} = 0 ----
         float vz[NC];
@@ -386,48 +485,15 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
                 for (int wd = 0; wd < W; wd++) {
                     const unsigned all = S.ymask[b * W + wd];
                     const unsigned fb = S.fbits[wd];
-                    // atoms without force moments, two per pass
-                    unsigned msk = need_dots ? (all & ~fb) : 0u;
-                    while (msk) {
-                        const int t0 = 32 * wd + __ffs(msk) - 1;
-                        msk &= msk - 1u;
-                        const bool two = msk != 0u;
-                        const int t1 = two ? 32 * wd + __ffs(msk) - 1 : t0;
-                        msk &= msk - 1u;
-                        const float4 *z0 = S.tz + t0 * (NZ / 2);
-                        const float4 *z1 = two ? S.tz + t1 * (NZ / 2) : S.zero;
-                        float G0a = 0.f, H0a = 0.f, G0b = 0.f, H0b = 0.f;
-                        float G1a = 0.f, H1a = 0.f, G1b = 0.f, H1b = 0.f;
-#pragma unroll
-                        for (int c = 0; c < NC; c += 2) {
-                            const float4 p0 = z0[c >> 1], p1 = z1[c >> 1];
-                            G0a += p0.x * vz[c];
-                            H0a += p0.y * vz[c];
-                            G1a += p1.x * vz[c];
-                            H1a += p1.y * vz[c];
-                            if (c + 1 < NC) {
-                                G0b += p0.z * vz[c + 1];
-                                H0b += p0.w * vz[c + 1];
-                                G1b += p1.z * vz[c + 1];
-                                H1b += p1.w * vz[c + 1];
-                            }
-                        }
-                        const float G0 = G0a + G0b, H0 = H0a + H0b, G1 = G1a + G1b, H1 = H1a + H1b;
-                        const float2 x0 = live ? S.tx[t0 * NC + a] : make_float2(0.f, 0.f);
-                        const float2 x1 = live ? S.tx[t1 * NC + a] : make_float2(0.f, 0.f);
-                        // per atom: g_x G -> s, hp_x G -> p_x, g_x H -> p_z (y factor g), g_x G -> p_y (y factor hp)
-                        const float v8[8] = {x0.x * G0, x0.y * G0, x0.x * H0, x0.x * G0,
-                                             x1.x * G1, x1.y * G1, x1.x * H1, x1.x * G1};
-                        const float red = reduce8(v8, lane);
-                        const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                        if ((lane & 3) == 0 && (idx < 4 || two)) {
-                            const int t = idx < 4 ? t0 : t1;
-                            const int comp = idx & 3;
-                            const float2 yv = S.ty[t * NC + b];
-                            S.slot[((size_t)b * amax + t) * 4 + (comp == 2 ? 3 : comp == 3 ? 2 : comp)] =
-                                (comp == 3 ? yv.y : yv.x) * red;
-                        }
+                    // atoms without force moments, two per pass, grouped by the half of the z range
+                    // their support covers
+                    if (need_dots) {
+                        const unsigned nf = all & ~fb, zl = S.zlo[wd], zh = S.zhi[wd];
+                        dots_pairs<NC, 0, kHalf + 1>(nf & zl, wd, S, vz, b, a, live, lane, amax);
+                        dots_pairs<NC, kHalf, NC>(nf & zh, wd, S, vz, b, a, live, lane, amax);
+                        dots_pairs<NC, 0, NC>(nf & ~(zl | zh), wd, S, vz, b, a, live, lane, amax);
                     }
+                    unsigned msk;
                     // atoms with force moments: projector and derivative contractions
                     msk = args.want_force ? (all & fb) : 0u;
                     while (msk) {
@@ -541,36 +607,10 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
             }
             // ---- KB term of Hhat v_k, from the dots ----
             for (int wd = 0; wd < W; wd++) {
-                unsigned msk = S.ymask[b * W + wd];
-                while (msk) {   // two atoms per pass
-                    const int t0 = 32 * wd + __ffs(msk) - 1;
-                    msk &= msk - 1u;
-                    const bool two = msk != 0u;
-                    const int t1 = two ? 32 * wd + __ffs(msk) - 1 : t0;
-                    msk &= msk - 1u;
-                    float A1[2], A2[2];
-#pragma unroll
-                    for (int i = 0; i < 2; i++) {
-                        const int t = i ? t1 : t0;
-                        const float4 s = *reinterpret_cast<const float4 *>(S.sd + 4 * t);
-                        const float2 yv = S.ty[t * NC + b];
-                        const float2 xv = live ? S.tx[t * NC + a] : make_float2(0.f, 0.f);
-                        // kappa_l chi (chi^T v) over s, p_x, p_y, p_z with the y factor folded in
-                        const float Pv = kap0 * s.x * yv.x + kap1 * s.z * yv.y;
-                        const float Qv = kap1 * s.w * yv.x;
-                        const float Rv = kap1 * s.y * yv.x;
-                        A1[i] = xv.x * Pv + xv.y * Rv;
-                        A2[i] = xv.x * Qv;
-                    }
-                    const float4 *z0 = S.tz + t0 * (NZ / 2);
-                    const float4 *z1 = two ? S.tz + t1 * (NZ / 2) : S.zero;
-#pragma unroll
-                    for (int c = 0; c < NC; c += 2) {
-                        const float4 p0 = z0[c >> 1], p1 = z1[c >> 1];
-                        w[c] += p0.x * A1[0] + p0.y * A2[0] + p1.x * A1[1] + p1.y * A2[1];
-                        if (c + 1 < NC) w[c + 1] += p0.z * A1[0] + p0.w * A2[0] + p1.z * A1[1] + p1.w * A2[1];
-                    }
-                }
+                const unsigned all = S.ymask[b * W + wd], zl = S.zlo[wd], zh = S.zhi[wd];
+                update_pairs<NC, 0, kHalf + 1>(all & zl, wd, S, w, b, a, live, kap0, kap1);
+                update_pairs<NC, kHalf, NC>(all & zh, wd, S, w, b, a, live, kap0, kap1);
+                update_pairs<NC, 0, NC>(all & ~(zl | zh), wd, S, w, b, a, live, kap0, kap1);
             }
             // ---- v_{k+1} = ca Hhat v_k - cb v_{k-1} ----
             const float ca = k == 0 ? 1.f : 2.f, cb = k == 0 ? 0.f : 1.f;
