@@ -295,6 +295,26 @@ def test_sq_error_decays_with_polynomial_order():
     assert errs[0] > errs[1] > errs[2] > errs[3]
 
 
+def test_truncated_sq_converges_with_cube_size():
+    """Truncation error against R_cut (Sec. 4, the convergence of the energy with the truncation
+    radius): on the 8-atom cell at a fixed K, the truncated SQ density, Fermi level, band energy and
+    forces approach the untruncated SQ values at the same K as the cube grows (m = 3..6, cubes
+    7^3..13^3), with the error falling by more than two decades over that range."""
+    c = cells.tiny_cell()
+    lo, hi = oracle.spectral_bounds(c)
+    ref = oracle.sq_solve(c, force=True, bounds=(lo, hi), full=True)
+    errs = []
+    for m in (3, 4, 5, 6):
+        c.R_cut = float(m * np.mean(c.h))
+        assert np.all(c.m == m)
+        r = oracle.sq_solve(c, force=True, bounds=(lo, hi))
+        errs.append((np.max(np.abs(r["rho"] - ref["rho"])) / np.max(ref["rho"]), abs(r["lam_f"] - ref["lam_f"]),
+                     abs(r["U"] - ref["U"]), np.max(np.abs(r["force"] - ref["force"]))))
+    errs = np.array(errs)
+    assert np.all(np.diff(errs, axis=0) < 0), errs
+    assert np.all(errs[-1] < 1e-2 * errs[0]), errs
+
+
 def test_hellmann_feynman_density():
     """dF/dV_eff(x_p) = rho(x_p) dV for F = U - kT S at fixed N_e (dense, exact)."""
     c = pin_cell(lmax=1, kT=0.05)
