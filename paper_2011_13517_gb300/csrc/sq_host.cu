@@ -1761,9 +1761,45 @@ static sq_status density_vjp(sq_handle h, const double *d_rho_bar, double U_bar,
     a.adj_kc = kc;
     a.adj_inv_tau = 1.0 / h->tau;
     const int nsegs = (K + kc - 1) / kc;
-    const long long stride = (long long)(2 + 2 * nsegs + kc + 1 + 3) * h->nc3;
     int dev_smem = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+    if constexpr (sizeof(T) == 4) {
+        // FP32 on 21^3 / 25^3 cubes with the 12th-order stencil: the slab mapping of the forward kernel
+        if (h->natom > 0 && slab_supported(h->nc, h->p)) {
+            int *d_cnt = reinterpret_cast<int *>(h->d_small) + 40;
+            SQ_CUDA(cudaMemsetAsync(d_cnt, 0, 3 * sizeof(int), stream));
+            SQ_COUNT(1);
+            SQ_CUDA(slab_counts(a, d_cnt, h->num_sms, stream));
+            int cnt[2];
+            SQ_CUDA(cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, stream));
+            SQ_CUDA(cudaStreamSynchronize(stream));
+            const int amax = cnt[0] > 0 ? cnt[0] : 1;
+            const size_t sm = slab_smem_bytes(h->nc[0], amax, 1);
+            if (sm <= (size_t)dev_smem) {
+                const long long sstride = (long long)(2 * nsegs + kc + 4) * slab_vector_floats(h->nc[0]);
+                long long grid = h->num_sms;
+                if (grid > h->N_d) grid = h->N_d;
+                if ((s = ensure(&h->d_scratch, &h->scratch_cap, sizeof(T) * (size_t)sstride * grid))) {
+                    cudaFree(d_aux);
+                    return s;
+                }
+                a.scratch = reinterpret_cast<T *>(h->d_scratch);
+                SQ_COUNT(1);
+                cudaError_t e = launch_slab_adjoint(a, amax, (int)grid, sm, d_cnt + 2, sstride, stream);
+                if (e != cudaSuccess) {
+                    cudaFree(d_aux);
+                    return fail(SQ_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(e));
+                }
+                int slab_err = 0;
+                SQ_CUDA(cudaMemcpyAsync(&slab_err, d_cnt + 2, sizeof(int), cudaMemcpyDeviceToHost, stream));
+                SQ_CUDA(cudaStreamSynchronize(stream));
+                cudaFree(d_aux);
+                if (slab_err) return fail(SQ_ERR_UNSUPPORTED, "a column exceeded the slab kernel's atom capacity (%d)", slab_err);
+                return SQ_OK;
+            }
+        }
+    }
+    const long long stride = (long long)(2 + 2 * nsegs + kc + 1 + 3) * h->nc3;
     const size_t smem = recursion_smem_bytes<T>(h->natom, h->nc, 0);
     if (smem > (size_t)dev_smem) { cudaFree(d_aux); return fail(SQ_ERR_UNSUPPORTED, "too many atoms for shared memory"); }
     long long grid = 2LL * h->num_sms;

@@ -107,5 +107,11 @@ size_t slab_smem_bytes(int nc, int amax, int fmax);
 cudaError_t slab_counts(const RecursionArgs<float> &args, int *d_counts, int num_sms, cudaStream_t stream);
 cudaError_t launch_slab(const RecursionArgs<float> &args, int amax, int fmax, int grid, size_t smem, int *err,
                         cudaStream_t stream);
+// Reverse-mode pass with the slab mapping (args.adj_* set, args.want_force = 0): per-CTA scratch of
+// scratch_stride floats = (2 nsegs + kc + 4) vectors of slab_vector_floats(nc) each; shared memory
+// slab_smem_bytes(nc, amax, 1).
+cudaError_t launch_slab_adjoint(const RecursionArgs<float> &args, int amax, int grid, size_t smem, int *err,
+                                long long scratch_stride, cudaStream_t stream);
+long long slab_vector_floats(int nc);
 
 }  // namespace sq

@@ -4,8 +4,9 @@ CPU: the oracle's forward-mode tangent (differentiated Chebyshev recursion plus 
 level term) against central finite differences of the oracle itself.
 GPU: the reverse-mode product (sq_density_vjp, reverse Clenshaw with checkpoints) against that
 tangent through the dot-product identity <rho_bar, d rho> + U_bar dU = <V_bar, dV>, against
-pointwise tangents, across checkpoint intervals, through the torch.autograd.Function, and at the
-full size of the 95-atom vacancy cell (K = 60)."""
+pointwise tangents, across checkpoint intervals, through the torch.autograd.Function, at the full
+size of the 95-atom vacancy cell (K = 60), and in FP32 on a 21^3-cube cell (the slab mapping)
+against the FP64 reverse mode."""
 import numpy as np
 import pytest
 
@@ -157,3 +158,28 @@ def test_vjp_vacancy_cell_full_size():
     print("vacancy VJP directional derivative: FD", fd, "FP64", ad64, "FP32", ad32)
     assert abs(ad64 - fd) < 1e-6 * abs(fd)
     assert abs(ad32 - fd) < 1e-3 * abs(fd)
+
+
+@gpu
+def test_fp32_slab_vjp_matches_fp64_on_21_cube():
+    """FP32 reverse mode on a 47-atom cell with 21^3 cubes (the slab mapping of the recursion) against
+    the FP64 reverse mode, which the dot-product tests hold to the oracle tangent: pointwise within
+    2e-4 of the largest component, for checkpoint intervals 1, 5 and 12 (single-step segments,
+    segments with recomputation, one segment), which agree with each other to 1e-6."""
+    _torch()
+    from paper_2011_13517_gb300 import sq
+    c = cells.make_cell("rc5", (3, 2, 2), 0.5, 12, 1, 5.0, 12, 0.005, seed=9, n_vacancy=1)
+    assert np.all(c.n_c == 21)
+    bounds = oracle.spectral_bounds(c)
+    rng = np.random.default_rng(21)
+    rho_bar = rng.standard_normal(c.N_d)
+    U_bar = 0.3
+    v64 = gpu_vjp(c, bounds, rho_bar, U_bar, 4, precision=sq.SQ_FP64)
+    scale = np.max(np.abs(v64))
+    v32 = {kc: gpu_vjp(c, bounds, rho_bar, U_bar, kc, precision=sq.SQ_FP32) for kc in (1, 5, 12)}
+    err = {kc: float(np.max(np.abs(v - v64)) / scale) for kc, v in v32.items()}
+    print("FP32 slab VJP max error / max |Vbar|:", err)
+    for kc in (1, 5, 12):
+        assert err[kc] < 2e-4
+    for kc in (1, 12):
+        np.testing.assert_allclose(v32[kc], v32[5], rtol=0, atol=1e-6 * scale)
