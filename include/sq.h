@@ -233,13 +233,15 @@ sq_status sq_moments_noalloc(sq_handle h, int K, int precision, void *d_mu, void
  * column -- a_K = mubar_K e_q, a_k = 2 Hhat_q a_{k+1} - a_{k+2} + mubar_k e_q (reverse Clenshaw) --
  * with the forward vectors stored as checkpoint pairs every checkpoint_k steps and recomputed segment
  * by segment (Eq. Chebyshev run backwards; the paper needs this derivative only implicitly, through
- * the SCF mixing of V_eff, Sec. 3).  Same recursion precision as the last sq_density.
+ * the SCF mixing of V_eff, Sec. 3).  Same recursion precision as the last sq_density; in SQ_FP32 on
+ * cubic 21^3 / 25^3 cubes with the 12th-order stencil it runs on the FP32 slab kernel's mapping.
  *   d_rho_bar    device [N_d] FP64 cotangent of rho (per bohr^3 density, as returned by sq_density)
  *   U_bar        cotangent of the band energy U
  *   checkpoint_k 1 <= checkpoint_k <= K (1: every vector kept; larger: less memory, more recompute)
  *   d_veff_bar   device [N_d] FP64 output (overwritten)
  * Column contributions are summed with FP64 atomics, so results may differ in the last bits between
- * runs.  Errors: SQ_ERR_STATE (no sq_density), SQ_ERR_ARG, SQ_ERR_OOM, SQ_ERR_CUDA.  Synchronises `stream`.
+ * runs.  Errors: SQ_ERR_STATE (no sq_density), SQ_ERR_ARG, SQ_ERR_OOM, SQ_ERR_UNSUPPORTED (a cube
+ * holds more atoms than shared memory allows), SQ_ERR_CUDA.  Synchronises `stream`.
  */
 sq_status sq_density_vjp(sq_handle h, const double *d_rho_bar, double U_bar, int checkpoint_k,
                          double *d_veff_bar, void *stream);
