@@ -34,6 +34,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # FP64 roofline: the nominal GB300 FP64 rate (1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 1.25
+# DRAM bytes (read + write) of one full-size vacancy launch, from one ncu capture of the same kernel
+# version (profiles/slab_kernel_fp32_vacancy.md: 3.41 MB read + 846.59 KB written); a kernel without
+# a capture of its current version reports null
+MEASURED_TRAFFIC = {"slab_kernel<25,6>": 3.41e6 + 846.59e3}
 
 
 def workload_config(cell):
@@ -444,7 +448,7 @@ def main():
                           rho=rho_out, force=force_out,
                           S=res[2], value=world * cell.N_d / (ms * 1e-3),
                           roofline={"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                                    "frac": achieved / peak, "traffic": None,
+                                    "frac": achieved / peak, "traffic": MEASURED_TRAFFIC.get(res[4]),
                                     "kernel": res[4],
                                     "algorithmic_tflop_per_launch": flops / 1e12,
                                     "kernel_ms": rec_ms,
