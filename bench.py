@@ -35,8 +35,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # FP64 roofline: the nominal GB300 FP64 rate (1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) of one full-size vacancy launch, from one ncu capture of the same kernel
-# version (profiles/slab_kernel_fp32_vacancy.md: 3.41 MB read + 846.59 KB written); a kernel without
-# a capture of its current version reports null
+# version (dram__bytes_read.sum 3.41 MB + dram__bytes_write.sum 846.59 KB); a kernel without a
+# capture of its current version reports null
 MEASURED_TRAFFIC = {"slab_kernel<25,6>": 3.41e6 + 846.59e3}
 
 

@@ -20,7 +20,7 @@
  *  - the nonlocal-force moments A_k^{J,lm,d} = sum_q chi_Jlm(x_q) sum_x d_d chi_Jlm(x) v_k^q(x)
  *    (Eq. NLforceSQ and the discrete nonlocal force of Sec. 3 "Atomic forces").
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent or ambiguous:
  *  - the recursion starts from the Euclidean unit vector e_q, so mu_0 = 1;
  *  - the discrete KB term carries dV, because chi^T v approximates the integral of chi f;
  *  - projectors are separable windowed Gaussians (below), summed over periodic images;
