@@ -176,9 +176,15 @@ def cpu_baseline(cell, target_seconds=15.0):
     t0 = time.perf_counter()
     oracle.moments(cell, omega, tau, cols=cols, force=True)
     dt = time.perf_counter() - t0
-    return {"value": ncols / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+    # the same oracle on one core, on a sample of about a quarter of the time
+    n1 = max(2, int(0.25 * target_seconds * ncols / dt / threads))
+    t0 = time.perf_counter()
+    oracle.moments(cell, omega, tau, cols=cols[:n1], force=True, nthreads=1)
+    one_core = n1 / (time.perf_counter() - t0)
+    return {"value": ncols / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "value_one_core": one_core,
             "sample": f"{ncols} random columns of the {cell.N_d}-point workload (moments + force moments, "
-                      f"K={cell.K}); Fermi solve and observables are O(K M) per step and not sampled",
+                      f"K={cell.K}; one-core figure on the first {n1} of them); Fermi solve and observables are "
+                      f"O(K M) per step and not sampled",
             "seconds": dt}
 
 
