@@ -131,14 +131,77 @@ sq_status sq_density(sq_handle h, int K, double kT, double N_e, int precision, i
                      double *d_rho, double *lambda_f, void *stream);
 
 /*
- * sq_fermi_level -- re-solve the electron-count equation (Eq. Ne) for a new kT / N_e from the
- * moment sums stored by the last sq_density, and refresh the stored weights; d_rho (may be NULL)
- * receives the matching density.  Same bisection rule as sq_density.
- * Errors: SQ_ERR_STATE (no sq_density yet), SQ_ERR_ARG, SQ_ERR_NO_BRACKET, SQ_ERR_CUDA.
+ * sq_fermi_level -- the Fermi level from moment sums (Eq. Ne, Sec. 3): solve
+ *     N(lambda_f) = 2 sum_k c_k(lambda_f) M_k = N_e
+ * on the host in FP64, where c_k(lambda_f) are the Chebyshev weights of the Fermi-Dirac function
+ * (Eq. ChebyshevWeights, M-point Chebyshev-Gauss quadrature as in sq_density), by bisection on
+ * [lambda_min, lambda_max]: mid = lo + (hi - lo)/2, lo = mid if N(mid) < N_e else hi = mid, until the
+ * midpoint no longer separates the bracket (at most 200 steps).  A pure function: no handle, no GPU.
+ * The paper does this with one global reduction of the moment sums over all processes; a caller that
+ * splits the columns (sq_moments_range) sums the M_k itself and solves here.
+ *   msum        host [K+1] moment sums M_k = sum_q mu_k^q over all grid points
+ *   K           polynomial order, 1 <= K <= 4096
+ *   omega, tau  scale and shift of the recursion (omega = (lambda_max+lambda_min)/2 and
+ *               tau = (lambda_max-lambda_min)/2 of the bounds the moments were computed with)
+ *   lambda_min, lambda_max   bisection bracket (normally the same spectral bounds)
+ *   kT, N_e     smearing (Ha, > 0) and electron count (> 0)
+ *   lambda_f    host output
+ * Errors: SQ_ERR_ARG, SQ_ERR_NOT_FINITE (a moment sum), SQ_ERR_NO_BRACKET (N(lambda_min) > N_e or
+ * N(lambda_max) < N_e), SQ_ERR_UNSUPPORTED (kT/tau needs more than 2^26 nodes).
+ */
+sq_status sq_fermi_level(const double *msum, int K, double omega, double tau, double lambda_min,
+                         double lambda_max, double kT, double N_e, double *lambda_f);
+
+/*
+ * sq_fermi_weights -- the Chebyshev weights at a given Fermi level (Eq. ChebyshevWeights, FP64, host):
+ * c_k of g(lam) (Eq. FermiDirac), d_k of lam g(lam) and e_k of s(g(lam)), k = 0..K, each a_k =
+ * (2 - delta_k0)/M sum_j f(lam_j) cos(k theta_j) over the M Chebyshev-Gauss nodes of sq_density.
+ * Then rho^q = 2 sum_k c_k mu_k^q, U = 2 sum_k d_k M_k and S = -2 sum_k e_k M_k (Eqs. rhoq, uq, sq).
+ * Outputs are host [K+1] arrays; any may be NULL.  Errors: SQ_ERR_ARG, SQ_ERR_UNSUPPORTED.
+ */
+sq_status sq_fermi_weights(double lambda_f, int K, double omega, double tau, double kT, double *c, double *d,
+                           double *e);
+
+/*
+ * sq_fermi_resolve -- re-solve the electron-count equation (Eq. Ne) for a new kT / N_e from the
+ * moment sums stored by the last whole-grid sq_density, on the device, and refresh the stored weights;
+ * d_rho (may be NULL) receives the matching density.  Same bisection rule as sq_density.
+ * Errors: SQ_ERR_STATE (no whole-grid sq_density yet), SQ_ERR_ARG, SQ_ERR_NO_BRACKET, SQ_ERR_CUDA.
  * Synchronises `stream`.
  */
-sq_status sq_fermi_level(sq_handle h, double kT, double N_e, double *d_rho, double *lambda_f,
-                         void *stream);
+sq_status sq_fermi_resolve(sq_handle h, double kT, double N_e, double *d_rho, double *lambda_f, void *stream);
+
+/*
+ * Column-range (sharded) form of sq_density.  The columns of the grid are independent given V_eff
+ * (Sec. 3 "Hamiltonian at each grid point": each point's cube needs only V_eff around it), and the
+ * Fermi level couples them through one global sum of moments (Eq. Ne).  A caller that splits the
+ * grid over processes or GPUs runs, per shard:
+ *     sq_moments_range  -> partial sums M_k (and force moments A) of its columns
+ *     (caller)          -> sum M_k and A over the shards (e.g. one allreduce)
+ *     sq_fermi_level    -> lambda_f (host, pure)
+ *     sq_observables    -> rho of its columns; then sq_energy and sq_nonlocal_force as usual.
+ *
+ * sq_moments_range -- the recursion (Eq. Chebyshev) for the columns q in [q_begin, q_end) only.
+ *   K, precision, flags   as sq_density (flags: 0 or SQ_WANT_FORCE)
+ *   q_begin, q_end        0 <= q_begin < q_end <= N_d
+ *   msum        host [K+1] output: M_k summed over the range's columns (FP64)
+ *   A           host [K+1][natom][nproj][3] output of the range's force moments
+ *               (required with SQ_WANT_FORCE, else ignored)
+ * Errors: SQ_ERR_ARG, SQ_ERR_NOT_FINITE, SQ_ERR_OOM, SQ_ERR_UNSUPPORTED, SQ_ERR_CUDA.  Synchronises
+ * `stream`.
+ *
+ * sq_observables -- after sq_moments_range, take the global sums and the Fermi level: stores msum
+ * (host [K+1] total M_k) and A (host total force moments, or NULL to skip forces), forms the weights
+ * at lambda_f (as sq_fermi_weights) and writes d_rho (device [q_end - q_begin] FP64, the density of
+ * the range's columns, rho(x_q) = 2 sum_k c_k mu_k^q / dV; may be NULL).  Afterwards sq_energy
+ * reports U, S, F from the total sums, and sq_nonlocal_force the forces from the total A.
+ * Errors: SQ_ERR_STATE (no sq_moments_range), SQ_ERR_ARG, SQ_ERR_NOT_FINITE, SQ_ERR_CUDA.
+ * Synchronises `stream`.
+ */
+sq_status sq_moments_range(sq_handle h, int K, int precision, int flags, long long q_begin, long long q_end,
+                           double *msum, double *A, void *stream);
+sq_status sq_observables(sq_handle h, double lambda_f, double kT, double N_e, const double *msum, const double *A,
+                         double *d_rho, void *stream);
 
 /*
  * sq_energy -- band energy U = 2 Tr(gamma H) = 2 sum_k d_k M_k (d_k: Chebyshev weights of lam g),
@@ -193,6 +256,15 @@ const char *sq_kernel_name(sq_handle h);
 
 /* Total number of kernels this library has launched in this process (for launch accounting). */
 long long sq_kernel_launches(void);
+
+/*
+ * sq_fma_throughput -- measured fused-multiply-add ceiling of the current GPU in the given precision
+ * (SQ_FP32 or SQ_FP64): a probe kernel of independent FMA chains at full occupancy on every SM, timed
+ * with CUDA events on `stream` (about 100 ms).  The recursion kernels are bound by these pipes, so
+ * this is the denominator of their roofline fraction.  Outputs: TFLOP/s (2 FLOP per FMA) and the
+ * timed launch's milliseconds (either may be NULL).  Errors: SQ_ERR_ARG, SQ_ERR_CUDA.
+ */
+sq_status sq_fma_throughput(int precision, double *tflops, double *ms, void *stream);
 
 /*
  * sq_moments_noalloc -- the Chebyshev moments mu_k^q (k = 0..K, every grid point) of the handle's

@@ -43,6 +43,8 @@ static long long g_launches = 0;
 
 extern "C" long long sq_kernel_launches(void) { return g_launches; }
 
+void sq::count_launches(long long n) { g_launches += n; }
+
 extern "C" const char *sq_status_string(sq_status s)
 {
     switch (s) {
@@ -90,6 +92,8 @@ struct sq_handle_s {
     double *d_small = nullptr;      // small scratch: reductions, bisection state
     // density state
     int have_density = 0, K = 0, precision = 0, have_force = 0;
+    int have_moments = 0;           // moments of columns [q0, q1) are in d_mu, their sums in d_msum
+    long long q0 = 0, q1 = 0;
     double kT = 0, N_e = 0, lam_f = 0;
     int M = 0;
     void *d_mu = nullptr;
@@ -307,11 +311,11 @@ __global__ void k_dpad(const double *veff, int n0, int n1, int n2, int m0, int m
 constexpr int kSumBlocks = 64;
 
 template <typename T>
-__global__ void k_msum_partial(const T *mu, long long N_d, int K, double *part)
+__global__ void k_msum_partial(const T *mu, long long N_d, int K, double *part, long long q0, long long q1)
 {
     const int k = blockIdx.y;
     double s = 0.0;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N_d; q += (long long)gridDim.x * blockDim.x)
+    for (long long q = q0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; q < q1; q += (long long)gridDim.x * blockDim.x)
         s += (double)mu[(size_t)k * N_d + q];
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -460,17 +464,18 @@ __global__ void k_coeffs(const double *f0, const double *f1, const double *f2, i
     }
 }
 
-// rho(x_q) = 2 sum_k c_k mu_k^q / dV
+// rho(x_q) = 2 sum_k c_k mu_k^q / dV for q in [q0, q1), written to rho[q - q0]
 template <typename T>
-__global__ void k_density(const T *mu, long long N_d, int K, const double *c, double inv_dV, double *rho)
+__global__ void k_density(const T *mu, long long N_d, int K, const double *c, double inv_dV, double *rho,
+                          long long q0, long long q1)
 {
     __shared__ double cs[512];
     for (int k = threadIdx.x; k <= K && k < 512; k += blockDim.x) cs[k] = c[k];
     __syncthreads();
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N_d; q += (long long)gridDim.x * blockDim.x) {
+    for (long long q = q0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; q < q1; q += (long long)gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int k = 0; k <= K; k++) s += (k < 512 ? cs[k] : c[k]) * (double)mu[(size_t)k * N_d + q];
-        rho[q] = 2.0 * s * inv_dV;
+        rho[q - q0] = 2.0 * s * inv_dV;
     }
 }
 
@@ -739,7 +744,47 @@ extern "C" void sq_destroy(sq_handle h)
 }
 
 template <typename T>
-static sq_status run_recursion(sq_handle h, int K, int want_force, cudaStream_t stream)
+static void fill_args(sq_handle h, int K, int want_force, RecursionArgs<T> &a)
+{
+    memset(&a, 0, sizeof(a));
+    for (int i = 0; i < 3; i++) {
+        a.n[i] = h->n[i];
+        a.m[i] = h->m[i];
+        a.nc[i] = h->nc[i];
+        a.pn[i] = h->pn[i];
+        a.fac_off[i] = h->fac2_off[i];
+        a.fac64_off[i] = h->fac64_off[i];
+        for (int j = 1; j <= h->p; j++) a.w[i][j - 1] = (T)(-h->fd[j] / (2.0 * h->h[i] * h->h[i] * h->tau));
+    }
+    a.nc3 = h->nc3;
+    a.N_d = h->N_d;
+    a.q0 = 0;
+    a.q1 = h->N_d;
+    a.K = K;
+    a.natom = h->natom;
+    a.nproj = h->nproj;
+    a.want_force = want_force;
+    if constexpr (sizeof(T) == 8) {
+        a.dpad = reinterpret_cast<const T *>(h->d_dpad64);
+        a.fac = reinterpret_cast<const T *>(h->d_fac2_64);
+    } else {
+        a.dpad = reinterpret_cast<const T *>(h->d_dpad32);
+        a.fac = reinterpret_cast<const T *>(h->d_fac2_32);
+    }
+    a.kappa[0] = (T)(h->cl[0] * h->dV * h->Nnorm * h->Nnorm / h->tau);
+    a.kappa[1] = (T)(h->cl[1] * h->dV * h->Nnorm * h->Nnorm / h->tau);
+    a.fac_stride = h->fac2_stride;
+    a.fac64 = h->d_fac64;
+    a.fac64_stride = h->fac64_stride;
+    a.sup_start = h->d_sup;
+    a.sup_len = h->d_sup + 3 * (h->natom > 0 ? h->natom : 1);
+    a.Nnorm = h->Nnorm;
+    a.mu = reinterpret_cast<T *>(h->d_mu);
+    a.A = want_force ? h->d_A : nullptr;
+}
+
+template <typename T>
+static sq_status run_recursion(sq_handle h, int K, int want_force, long long q0, long long q1, cudaStream_t stream)
 {
     sq_status s;
     const size_t pad = (size_t)h->pn[0] * h->pn[1] * h->pn[2];
@@ -756,35 +801,10 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, cudaStream_t 
     SQ_CUDA(cudaGetLastError());
 
     RecursionArgs<T> a;
-    memset(&a, 0, sizeof(a));
-    for (int i = 0; i < 3; i++) {
-        a.n[i] = h->n[i];
-        a.m[i] = h->m[i];
-        a.nc[i] = h->nc[i];
-        a.pn[i] = h->pn[i];
-        a.fac_off[i] = h->fac2_off[i];
-        a.fac64_off[i] = h->fac64_off[i];
-        for (int j = 1; j <= h->p; j++) a.w[i][j - 1] = (T)(-h->fd[j] / (2.0 * h->h[i] * h->h[i] * h->tau));
-    }
-    a.nc3 = h->nc3;
-    a.N_d = h->N_d;
-    a.K = K;
-    a.natom = h->natom;
-    a.nproj = h->nproj;
-    a.want_force = want_force;
+    fill_args<T>(h, K, want_force, a);
     a.dpad = *dpad;
-    a.kappa[0] = (T)(h->cl[0] * h->dV * h->Nnorm * h->Nnorm / h->tau);
-    a.kappa[1] = (T)(h->cl[1] * h->dV * h->Nnorm * h->Nnorm / h->tau);
-    if constexpr (sizeof(T) == 8) a.fac = reinterpret_cast<const T *>(h->d_fac2_64);
-    else a.fac = reinterpret_cast<const T *>(h->d_fac2_32);
-    a.fac_stride = h->fac2_stride;
-    a.fac64 = h->d_fac64;
-    a.fac64_stride = h->fac64_stride;
-    a.sup_start = h->d_sup;
-    a.sup_len = h->d_sup + 3 * (h->natom > 0 ? h->natom : 1);
-    a.Nnorm = h->Nnorm;
-    a.mu = reinterpret_cast<T *>(h->d_mu);
-    a.A = want_force ? h->d_A : nullptr;
+    a.q0 = q0;
+    a.q1 = q1;
 
     int dev_smem = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
@@ -803,7 +823,7 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, cudaStream_t 
             const size_t sm = slab_smem_bytes(h->nc[0], amax, fmax);
             if (sm <= (size_t)dev_smem) {
                 long long grid = h->num_sms;
-                if (grid > h->N_d) grid = h->N_d;
+                if (grid > q1 - q0) grid = q1 - q0;
                 h->kernel_used = 1;
                 SQ_CUDA(cudaEventRecord(h->ev[0], stream));
                 SQ_COUNT(1);
@@ -812,7 +832,7 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, cudaStream_t 
                 dim3 g2(kSumBlocks, K + 1);
                 SQ_COUNT(1);
                 k_msum_partial<T><<<g2, 256, 0, stream>>>(reinterpret_cast<const T *>(h->d_mu), h->N_d, K,
-                                                          h->d_msum_part);
+                                                          h->d_msum_part, q0, q1);
                 SQ_CUDA(cudaGetLastError());
                 return SQ_OK;
             }
@@ -836,7 +856,7 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, cudaStream_t 
     int per_sm = recursion_blocks_per_sm<T>(h->p, block, smem, a.vec_in_smem);
     if (per_sm < 1) return fail(SQ_ERR_UNSUPPORTED, "recursion kernel does not fit on an SM");
     long long grid = (long long)per_sm * h->num_sms;
-    if (grid > h->N_d) grid = h->N_d;
+    if (grid > q1 - q0) grid = q1 - q0;
     if (!a.vec_in_smem) {
         if ((s = ensure(&h->d_scratch, &h->scratch_cap, sizeof(T) * 2 * (size_t)h->nc3 * grid))) return s;
         a.scratch = reinterpret_cast<T *>(h->d_scratch);
@@ -848,9 +868,60 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, cudaStream_t 
     // moment sums
     dim3 g2(kSumBlocks, K + 1);
     SQ_COUNT(1);
-    k_msum_partial<T><<<g2, 256, 0, stream>>>(reinterpret_cast<const T *>(h->d_mu), h->N_d, K, h->d_msum_part);
+    k_msum_partial<T><<<g2, 256, 0, stream>>>(reinterpret_cast<const T *>(h->d_mu), h->N_d, K, h->d_msum_part,
+                                              q0, q1);
     SQ_CUDA(cudaGetLastError());
     return SQ_OK;
+}
+
+// Number of Chebyshev-Gauss nodes of the weight quadrature: M = 2^ceil(log2 max(4(K+1), 16 tau/kT)),
+// or 0 when that exceeds 2^26.
+static int fermi_nodes(int K, double tau, double kT)
+{
+    const double need = fmax(4.0 * (K + 1), 16.0 * tau / kT);
+    int M = 1;
+    while (M < need && M <= (1 << 26)) M <<= 1;
+    return M > (1 << 26) ? 0 : M;
+}
+
+// Node arrays (lambda_j, D_j) from the stored moment sums, sized for (K, kT).
+static sq_status nodes_at(sq_handle h, double kT, int *M_out, cudaStream_t stream)
+{
+    const int K = h->K;
+    const int M = fermi_nodes(K, h->tau, kT);
+    if (!M) return fail(SQ_ERR_UNSUPPORTED, "kT/tau too small for the weight quadrature");
+    sq_status s;
+    if ((s = ensure(&h->d_nodes, &h->nodes_cap, sizeof(double) * 5 * (size_t)M))) return s;
+    if ((s = ensure(&h->d_coef, &h->coef_cap, sizeof(double) * 3 * (size_t)(K + 1)))) return s;
+    SQ_COUNT(1);
+    k_nodes<<<grid_for(M, 256, h->num_sms), 256, 0, stream>>>(h->d_msum, K, M, h->omega, h->tau, h->d_nodes,
+                                                               h->d_nodes + M);
+    SQ_CUDA(cudaGetLastError());
+    *M_out = M;
+    return SQ_OK;
+}
+
+// Chebyshev weights c_k, d_k, e_k of g, lam g and s(g) at the Fermi level lf (nodes already set).
+static sq_status coeffs_at(sq_handle h, int M, double lf, double kT, cudaStream_t stream)
+{
+    const int K = h->K;
+    double *lam = h->d_nodes, *f0 = h->d_nodes + 2 * M, *f1 = h->d_nodes + 3 * M, *f2 = h->d_nodes + 4 * M;
+    SQ_COUNT(2);
+    k_node_functions<<<grid_for(M, 256, h->num_sms), 256, 0, stream>>>(lam, M, lf, kT, f0, f1, f2);
+    SQ_CUDA(cudaGetLastError());
+    k_coeffs<<<dim3(K + 1, 3), 256, 0, stream>>>(f0, f1, f2, M, K, h->d_coef);
+    SQ_CUDA(cudaGetLastError());
+    h->M = M;
+    return SQ_OK;
+}
+
+// Weights at a given Fermi level (the level itself solved elsewhere).
+static sq_status weights_at(sq_handle h, double lf, double kT, cudaStream_t stream)
+{
+    int M = 0;
+    sq_status s;
+    if ((s = nodes_at(h, kT, &M, stream))) return s;
+    return coeffs_at(h, M, lf, kT, stream);
 }
 
 // Fermi level, weights and (optionally) the density from the stored moment sums.
@@ -858,20 +929,11 @@ static sq_status fermi_and_density(sq_handle h, double kT, double N_e, double *d
                                    cudaStream_t stream)
 {
     const int K = h->K;
-    // M = 2^ceil(log2 max(4(K+1), 16 tau/kT))
-    const double need = fmax(4.0 * (K + 1), 16.0 * h->tau / kT);
-    int M = 1;
-    while (M < need) M <<= 1;
-    if (M > (1 << 26)) return fail(SQ_ERR_UNSUPPORTED, "kT/tau too small: %d Chebyshev nodes", M);
-    sq_status s;
-    if ((s = ensure(&h->d_nodes, &h->nodes_cap, sizeof(double) * 5 * (size_t)M))) return s;
-    if ((s = ensure(&h->d_coef, &h->coef_cap, sizeof(double) * 3 * (size_t)(K + 1)))) return s;
-    double *lam = h->d_nodes, *D = h->d_nodes + M, *f0 = h->d_nodes + 2 * M, *f1 = h->d_nodes + 3 * M,
-           *f2 = h->d_nodes + 4 * M;
     SQ_CUDA(cudaEventRecord(h->ev[3], stream));
-    SQ_COUNT(1);
-    k_nodes<<<grid_for(M, 256, h->num_sms), 256, 0, stream>>>(h->d_msum, K, M, h->omega, h->tau, lam, D);
-    SQ_CUDA(cudaGetLastError());
+    int M = 0;
+    sq_status s;
+    if ((s = nodes_at(h, kT, &M, stream))) return s;
+    double *lam = h->d_nodes, *D = h->d_nodes + M;
     // bisection state lives in the small scratch (after the first 256 bytes)
     FermiState *st = reinterpret_cast<FermiState *>(reinterpret_cast<char *>(h->d_small) + 256);
     double *part = reinterpret_cast<double *>(reinterpret_cast<char *>(h->d_small) + 512);
@@ -894,19 +956,15 @@ static sq_status fermi_and_density(sq_handle h, double kT, double N_e, double *d
     if (fin.phase != 3) return fail(SQ_ERR_TIMEOUT, "bisection did not finish");
     const double lf = fin.x;
     if (!std::isfinite(lf)) return fail(SQ_ERR_NOT_FINITE, "Fermi level is not finite");
-    SQ_COUNT(2);
-    k_node_functions<<<grid_for(M, 256, h->num_sms), 256, 0, stream>>>(lam, M, lf, kT, f0, f1, f2);
-    SQ_CUDA(cudaGetLastError());
-    k_coeffs<<<dim3(K + 1, 3), 256, 0, stream>>>(f0, f1, f2, M, K, h->d_coef);
-    SQ_CUDA(cudaGetLastError());
+    if ((s = coeffs_at(h, M, lf, kT, stream))) return s;
     if (d_rho) {
         SQ_COUNT(1);
         if (h->precision == SQ_FP64)
             k_density<double><<<grid_for(h->N_d, 256, h->num_sms), 256, 0, stream>>>(
-                reinterpret_cast<const double *>(h->d_mu), h->N_d, K, h->d_coef, 1.0 / h->dV, d_rho);
+                reinterpret_cast<const double *>(h->d_mu), h->N_d, K, h->d_coef, 1.0 / h->dV, d_rho, 0LL, h->N_d);
         else
             k_density<float><<<grid_for(h->N_d, 256, h->num_sms), 256, 0, stream>>>(
-                reinterpret_cast<const float *>(h->d_mu), h->N_d, K, h->d_coef, 1.0 / h->dV, d_rho);
+                reinterpret_cast<const float *>(h->d_mu), h->N_d, K, h->d_coef, 1.0 / h->dV, d_rho, 0LL, h->N_d);
         SQ_CUDA(cudaGetLastError());
     }
     SQ_CUDA(cudaEventRecord(h->ev[4], stream));
@@ -914,24 +972,17 @@ static sq_status fermi_and_density(sq_handle h, double kT, double N_e, double *d
     h->kT = kT;
     h->N_e = N_e;
     h->lam_f = lf;
-    h->M = M;
     if (lambda_f) *lambda_f = lf;
     return SQ_OK;
 }
 
-extern "C" sq_status sq_density(sq_handle h, int K, double kT, double N_e, int precision, int flags, double *d_rho,
-                                double *lambda_f, void *stream_)
+// Recursion over columns [q0, q1), moments into the handle's [K+1][N_d] buffer, and the moment sums of
+// those columns into h->d_msum (FP64).  Leaves the handle without a density (have_density = 0).
+static sq_status moments_stage(sq_handle h, int K, int precision, int want_force, long long q0, long long q1,
+                               cudaStream_t stream)
 {
-    g_last_error[0] = 0;
-    if (!h || !d_rho || !lambda_f) return fail(SQ_ERR_ARG, "null argument");
-    if (K < 1 || K > 4096) return fail(SQ_ERR_ARG, "K = %d", K);
-    if (!(kT > 0) || !std::isfinite(kT)) return fail(SQ_ERR_ARG, "kT = %g", kT);
-    if (!(N_e > 0) || !(N_e < 2.0 * h->N_d)) return fail(SQ_ERR_ARG, "N_e = %g", N_e);
-    if (precision != SQ_FP64 && precision != SQ_FP32) return fail(SQ_ERR_ARG, "precision %d", precision);
-    if (flags & ~SQ_WANT_FORCE) return fail(SQ_ERR_ARG, "flags %d", flags);
-    cudaStream_t stream = (cudaStream_t)stream_;
-    const int want_force = (flags & SQ_WANT_FORCE) && h->natom > 0;
     h->have_density = 0;
+    h->have_moments = 0;
     sq_status s;
     const size_t esz = precision == SQ_FP64 ? 8 : 4;
     if ((s = ensure(&h->d_mu, &h->mu_bytes, esz * (size_t)(K + 1) * h->N_d))) return s;
@@ -944,8 +995,8 @@ extern "C" sq_status sq_density(sq_handle h, int K, double kT, double N_e, int p
     }
     h->precision = precision;
     h->K = K;
-    s = precision == SQ_FP64 ? run_recursion<double>(h, K, want_force, stream)
-                             : run_recursion<float>(h, K, want_force, stream);
+    s = precision == SQ_FP64 ? run_recursion<double>(h, K, want_force, q0, q1, stream)
+                             : run_recursion<float>(h, K, want_force, q0, q1, stream);
     if (s) return s;
     int *d_bad = reinterpret_cast<int *>(h->d_small);
     SQ_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), stream));
@@ -955,29 +1006,224 @@ extern "C" sq_status sq_density(sq_handle h, int K, double kT, double N_e, int p
     SQ_CUDA(cudaEventRecord(h->ev[2], stream));
     int bad = 0, slab_err = 0;
     SQ_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    if (h->kernel_used == 1)
+    if (h->kernel_used != 0)
         SQ_CUDA(cudaMemcpyAsync(&slab_err, reinterpret_cast<int *>(h->d_small) + 42, sizeof(int),
                                 cudaMemcpyDeviceToHost, stream));
     SQ_CUDA(cudaStreamSynchronize(stream));
     if (slab_err) return fail(SQ_ERR_UNSUPPORTED, "a column exceeded the slab kernel's atom capacity (%d)", slab_err);
     if (bad) return fail(SQ_ERR_NOT_FINITE, "moment sums are not finite");
-    if ((s = fermi_and_density(h, kT, N_e, d_rho, lambda_f, stream))) return s;
     SQ_CUDA(cudaEventElapsedTime(&h->t_rec, h->ev[0], h->ev[1]));
     SQ_CUDA(cudaEventElapsedTime(&h->t_msum, h->ev[1], h->ev[2]));
-    SQ_CUDA(cudaEventElapsedTime(&h->t_fermi, h->ev[3], h->ev[4]));
     h->have_force = want_force;
+    h->q0 = q0;
+    h->q1 = q1;
+    h->have_moments = 1;
+    return SQ_OK;
+}
+
+static sq_status check_density_args(sq_handle h, int K, double kT, double N_e, int precision, int flags)
+{
+    if (K < 1 || K > 4096) return fail(SQ_ERR_ARG, "K = %d", K);
+    if (!(kT > 0) || !std::isfinite(kT)) return fail(SQ_ERR_ARG, "kT = %g", kT);
+    if (!(N_e > 0) || !(N_e < 2.0 * h->N_d)) return fail(SQ_ERR_ARG, "N_e = %g", N_e);
+    if (precision != SQ_FP64 && precision != SQ_FP32) return fail(SQ_ERR_ARG, "precision %d", precision);
+    if (flags & ~SQ_WANT_FORCE) return fail(SQ_ERR_ARG, "flags %d", flags);
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_density(sq_handle h, int K, double kT, double N_e, int precision, int flags, double *d_rho,
+                                double *lambda_f, void *stream_)
+{
+    g_last_error[0] = 0;
+    if (!h || !d_rho || !lambda_f) return fail(SQ_ERR_ARG, "null argument");
+    sq_status s;
+    if ((s = check_density_args(h, K, kT, N_e, precision, flags))) return s;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int want_force = (flags & SQ_WANT_FORCE) && h->natom > 0;
+    if ((s = moments_stage(h, K, precision, want_force, 0, h->N_d, stream))) return s;
+    if ((s = fermi_and_density(h, kT, N_e, d_rho, lambda_f, stream))) return s;
+    SQ_CUDA(cudaEventElapsedTime(&h->t_fermi, h->ev[3], h->ev[4]));
     h->have_density = 1;
     return SQ_OK;
 }
 
-extern "C" sq_status sq_fermi_level(sq_handle h, double kT, double N_e, double *d_rho, double *lambda_f,
-                                    void *stream_)
+extern "C" sq_status sq_fermi_resolve(sq_handle h, double kT, double N_e, double *d_rho, double *lambda_f,
+                                      void *stream_)
 {
     g_last_error[0] = 0;
     if (!h || !lambda_f) return fail(SQ_ERR_ARG, "null argument");
-    if (!h->have_density) return fail(SQ_ERR_STATE, "sq_fermi_level before sq_density");
+    if (!h->have_density || h->q0 != 0 || h->q1 != h->N_d)
+        return fail(SQ_ERR_STATE, "sq_fermi_resolve needs a whole-grid sq_density first");
     if (!(kT > 0) || !(N_e > 0) || !(N_e < 2.0 * h->N_d)) return fail(SQ_ERR_ARG, "kT = %g, N_e = %g", kT, N_e);
     return fermi_and_density(h, kT, N_e, d_rho, lambda_f, (cudaStream_t)stream_);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Column-range form of the path (one shard of the grid), for callers that split the columns over
+// processes or GPUs and sum the moments themselves (Eq. Ne needs one global sum).
+
+extern "C" sq_status sq_moments_range(sq_handle h, int K, int precision, int flags, long long q_begin, long long q_end,
+                                      double *msum, double *A, void *stream_)
+{
+    g_last_error[0] = 0;
+    if (!h || !msum) return fail(SQ_ERR_ARG, "null argument");
+    if (K < 1 || K > 4096) return fail(SQ_ERR_ARG, "K = %d", K);
+    if (precision != SQ_FP64 && precision != SQ_FP32) return fail(SQ_ERR_ARG, "precision %d", precision);
+    if (flags & ~SQ_WANT_FORCE) return fail(SQ_ERR_ARG, "flags %d", flags);
+    if (q_begin < 0 || q_end > h->N_d || q_begin >= q_end)
+        return fail(SQ_ERR_ARG, "column range [%lld, %lld) of %lld", q_begin, q_end, h->N_d);
+    const int want_force = (flags & SQ_WANT_FORCE) && h->natom > 0;
+    if (want_force && !A) return fail(SQ_ERR_ARG, "SQ_WANT_FORCE needs the force-moment output A");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    sq_status s;
+    if ((s = moments_stage(h, K, precision, want_force, q_begin, q_end, stream))) return s;
+    SQ_CUDA(cudaMemcpyAsync(msum, h->d_msum, sizeof(double) * (K + 1), cudaMemcpyDeviceToHost, stream));
+    if (want_force)
+        SQ_CUDA(cudaMemcpyAsync(A, h->d_A, sizeof(double) * (size_t)(K + 1) * h->natom * h->nproj * 3,
+                                cudaMemcpyDeviceToHost, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_observables(sq_handle h, double lambda_f, double kT, double N_e, const double *msum,
+                                    const double *A, double *d_rho, void *stream_)
+{
+    g_last_error[0] = 0;
+    if (!h || !msum) return fail(SQ_ERR_ARG, "null argument");
+    if (!h->have_moments) return fail(SQ_ERR_STATE, "sq_observables before sq_moments_range");
+    if (!(kT > 0) || !std::isfinite(kT) || !std::isfinite(lambda_f) || !(N_e > 0))
+        return fail(SQ_ERR_ARG, "lambda_f = %g, kT = %g, N_e = %g", lambda_f, kT, N_e);
+    for (int k = 0; k <= h->K; k++)
+        if (!std::isfinite(msum[k])) return fail(SQ_ERR_NOT_FINITE, "moment sum %d", k);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int K = h->K;
+    h->have_density = 0;
+    SQ_CUDA(cudaMemcpyAsync(h->d_msum, msum, sizeof(double) * (K + 1), cudaMemcpyHostToDevice, stream));
+    const int force = h->have_force && A;
+    if (force)
+        SQ_CUDA(cudaMemcpyAsync(h->d_A, A, sizeof(double) * (size_t)(K + 1) * h->natom * h->nproj * 3,
+                                cudaMemcpyHostToDevice, stream));
+    sq_status s;
+    if ((s = weights_at(h, lambda_f, kT, stream))) return s;
+    if (d_rho) {
+        const long long n = h->q1 - h->q0;
+        SQ_COUNT(1);
+        if (h->precision == SQ_FP64)
+            k_density<double><<<grid_for(n, 256, h->num_sms), 256, 0, stream>>>(
+                reinterpret_cast<const double *>(h->d_mu), h->N_d, K, h->d_coef, 1.0 / h->dV, d_rho, h->q0, h->q1);
+        else
+            k_density<float><<<grid_for(n, 256, h->num_sms), 256, 0, stream>>>(
+                reinterpret_cast<const float *>(h->d_mu), h->N_d, K, h->d_coef, 1.0 / h->dV, d_rho, h->q0, h->q1);
+        SQ_CUDA(cudaGetLastError());
+    }
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    h->kT = kT;
+    h->N_e = N_e;
+    h->lam_f = lambda_f;
+    h->have_force = force;
+    h->have_density = 1;
+    return SQ_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Pure host form of the Fermi-level solve (Eq. Ne) and of the Chebyshev weights (Eq.
+// ChebyshevWeights), in FP64, for moment sums that were reduced outside the library.  Same node rule,
+// node functions and bisection rule as the device path.
+
+static double host_cos_k_theta(int k, int j, int M)
+{
+    // cos(k pi (2j+1)/(2M)) with exact argument reduction modulo 2 pi
+    const long long r = ((long long)k * (2LL * j + 1)) % (4LL * M);
+    return cos(M_PI * (double)r / (2.0 * M));
+}
+
+static double host_fermi_fn(double lam, double lam_f, double kT) { return 0.5 * (1.0 - tanh((lam - lam_f) / (2.0 * kT))); }
+
+static void host_node_lambdas(int M, double omega, double tau, std::vector<double> &lam)
+{
+    lam.resize(M);
+    for (int j = 0; j < M; j++) lam[j] = tau * cos(M_PI * (j + 0.5) / M) + omega;
+}
+
+static bool host_scalar_ok(double x) { return std::isfinite(x); }
+
+extern "C" sq_status sq_fermi_level(const double *msum, int K, double omega, double tau, double lambda_min,
+                                    double lambda_max, double kT, double N_e, double *lambda_f)
+{
+    g_last_error[0] = 0;
+    if (!msum || !lambda_f) return fail(SQ_ERR_ARG, "null argument");
+    if (K < 1 || K > 4096) return fail(SQ_ERR_ARG, "K = %d", K);
+    if (!(tau > 0) || !host_scalar_ok(omega) || !host_scalar_ok(tau)) return fail(SQ_ERR_ARG, "omega = %g, tau = %g", omega, tau);
+    if (!(lambda_max > lambda_min) || !host_scalar_ok(lambda_min) || !host_scalar_ok(lambda_max))
+        return fail(SQ_ERR_ARG, "bracket [%g, %g]", lambda_min, lambda_max);
+    if (!(kT > 0) || !host_scalar_ok(kT) || !(N_e > 0) || !host_scalar_ok(N_e))
+        return fail(SQ_ERR_ARG, "kT = %g, N_e = %g", kT, N_e);
+    for (int k = 0; k <= K; k++)
+        if (!host_scalar_ok(msum[k])) return fail(SQ_ERR_NOT_FINITE, "moment sum %d", k);
+    const int M = fermi_nodes(K, tau, kT);
+    if (!M) return fail(SQ_ERR_UNSUPPORTED, "kT/tau too small for the weight quadrature");
+    std::vector<double> lam, D(M);
+    host_node_lambdas(M, omega, tau, lam);
+    for (int j = 0; j < M; j++) {
+        double s = msum[0];
+        for (int k = 1; k <= K; k++) s += 2.0 * msum[k] * host_cos_k_theta(k, j, M);
+        D[j] = s / M;
+    }
+    auto count = [&](double x) {
+        double N = 0.0;
+        for (int j = 0; j < M; j++) N += host_fermi_fn(lam[j], x, kT) * D[j];
+        return 2.0 * N;
+    };
+    double lo = lambda_min, hi = lambda_max;
+    const double N_lo = count(lo), N_hi = count(hi);
+    if (N_lo > N_e || N_hi < N_e)
+        return fail(SQ_ERR_NO_BRACKET, "N(lambda_min) = %.6g, N(lambda_max) = %.6g, N_e = %.6g", N_lo, N_hi, N_e);
+    double x = lo + 0.5 * (hi - lo);
+    for (int iter = 1; iter <= 200; iter++) {
+        if (count(x) < N_e) lo = x;
+        else hi = x;
+        x = lo + 0.5 * (hi - lo);
+        if (x <= lo || x >= hi) break;
+    }
+    if (!host_scalar_ok(x)) return fail(SQ_ERR_NOT_FINITE, "Fermi level is not finite");
+    *lambda_f = x;
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_fermi_weights(double lambda_f, int K, double omega, double tau, double kT, double *c,
+                                      double *d, double *e)
+{
+    g_last_error[0] = 0;
+    if (K < 1 || K > 4096) return fail(SQ_ERR_ARG, "K = %d", K);
+    if (!(tau > 0) || !host_scalar_ok(omega) || !host_scalar_ok(tau) || !(kT > 0) || !host_scalar_ok(kT) ||
+        !host_scalar_ok(lambda_f))
+        return fail(SQ_ERR_ARG, "lambda_f = %g, omega = %g, tau = %g, kT = %g", lambda_f, omega, tau, kT);
+    const int M = fermi_nodes(K, tau, kT);
+    if (!M) return fail(SQ_ERR_UNSUPPORTED, "kT/tau too small for the weight quadrature");
+    std::vector<double> lam, f0(M), f1(M), f2(M);
+    host_node_lambdas(M, omega, tau, lam);
+    for (int j = 0; j < M; j++) {
+        const double l = lam[j];
+        const double g = host_fermi_fn(l, lambda_f, kT);
+        const double y = fabs((l - lambda_f) / kT);
+        f0[j] = g;
+        f1[j] = l * g;
+        f2[j] = -(log1p(exp(-y)) + y * host_fermi_fn(y, 0.0, 1.0));
+    }
+    for (int k = 0; k <= K; k++) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int j = 0; j < M; j++) {
+            const double ck = host_cos_k_theta(k, j, M);
+            s0 += f0[j] * ck;
+            s1 += f1[j] * ck;
+            s2 += f2[j] * ck;
+        }
+        const double w = (k == 0 ? 1.0 : 2.0) / M;
+        if (c) c[k] = w * s0;
+        if (d) d[k] = w * s1;
+        if (e) e[k] = w * s2;
+    }
+    return SQ_OK;
 }
 
 extern "C" sq_status sq_energy(sq_handle h, double *U, double *S, double *F, void *stream_)
@@ -1137,6 +1383,8 @@ static sq_status moments_noalloc(sq_handle h, int K, void *d_mu, cudaStream_t st
     }
     a.nc3 = h->nc3;
     a.N_d = h->N_d;
+    a.q0 = 0;
+    a.q1 = h->N_d;
     a.K = K;
     a.natom = h->natom;
     a.nproj = h->nproj;
@@ -1247,44 +1495,6 @@ struct sq_batch_s {
     std::vector<int> slab_amax, slab_fmax;
     std::vector<size_t> slab_smem;
 };
-
-template <typename T>
-static void fill_args(sq_handle h, int K, int want_force, RecursionArgs<T> &a)
-{
-    memset(&a, 0, sizeof(a));
-    for (int i = 0; i < 3; i++) {
-        a.n[i] = h->n[i];
-        a.m[i] = h->m[i];
-        a.nc[i] = h->nc[i];
-        a.pn[i] = h->pn[i];
-        a.fac_off[i] = h->fac2_off[i];
-        a.fac64_off[i] = h->fac64_off[i];
-        for (int j = 1; j <= h->p; j++) a.w[i][j - 1] = (T)(-h->fd[j] / (2.0 * h->h[i] * h->h[i] * h->tau));
-    }
-    a.nc3 = h->nc3;
-    a.N_d = h->N_d;
-    a.K = K;
-    a.natom = h->natom;
-    a.nproj = h->nproj;
-    a.want_force = want_force;
-    if constexpr (sizeof(T) == 8) {
-        a.dpad = reinterpret_cast<const T *>(h->d_dpad64);
-        a.fac = reinterpret_cast<const T *>(h->d_fac2_64);
-    } else {
-        a.dpad = reinterpret_cast<const T *>(h->d_dpad32);
-        a.fac = reinterpret_cast<const T *>(h->d_fac2_32);
-    }
-    a.kappa[0] = (T)(h->cl[0] * h->dV * h->Nnorm * h->Nnorm / h->tau);
-    a.kappa[1] = (T)(h->cl[1] * h->dV * h->Nnorm * h->Nnorm / h->tau);
-    a.fac_stride = h->fac2_stride;
-    a.fac64 = h->d_fac64;
-    a.fac64_stride = h->fac64_stride;
-    a.sup_start = h->d_sup;
-    a.sup_len = h->d_sup + 3 * (h->natom > 0 ? h->natom : 1);
-    a.Nnorm = h->Nnorm;
-    a.mu = reinterpret_cast<T *>(h->d_mu);
-    a.A = want_force ? h->d_A : nullptr;
-}
 
 extern "C" void sq_batch_destroy(sq_batch b)
 {
@@ -1481,7 +1691,8 @@ static sq_status batch_enqueue(sq_batch b, const RecursionArgs<T> *host_args, do
         SQ_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), stream));
         dim3 g2(kSumBlocks, K + 1);
         SQ_COUNT(2);
-        k_msum_partial<T><<<g2, 256, 0, stream>>>(reinterpret_cast<const T *>(h->d_mu), h->N_d, K, h->d_msum_part);
+        k_msum_partial<T><<<g2, 256, 0, stream>>>(reinterpret_cast<const T *>(h->d_mu), h->N_d, K, h->d_msum_part,
+                                              0LL, h->N_d);
         k_msum_final<<<1, 256, 0, stream>>>(h->d_msum_part, kSumBlocks, K, h->d_msum, d_bad);
         SQ_CUDA(cudaGetLastError());
         double *lam = h->d_nodes, *D = h->d_nodes + M, *f0 = h->d_nodes + 2 * M, *f1 = h->d_nodes + 3 * M,
@@ -1498,7 +1709,7 @@ static sq_status batch_enqueue(sq_batch b, const RecursionArgs<T> *host_args, do
         k_node_functions_state<<<grid_for(M, 256, h->num_sms), 256, 0, stream>>>(lam, M, st, b->kT[i], f0, f1, f2);
         k_coeffs<<<dim3(K + 1, 3), 256, 0, stream>>>(f0, f1, f2, M, K, h->d_coef);
         k_density<T><<<grid_for(h->N_d, 256, h->num_sms), 256, 0, stream>>>(reinterpret_cast<const T *>(h->d_mu),
-                                                                           h->N_d, K, h->d_coef, 1.0 / h->dV, d_rho[i]);
+                                                                           h->N_d, K, h->d_coef, 1.0 / h->dV, d_rho[i], 0LL, h->N_d);
         SQ_CUDA(cudaGetLastError());
     }
     return SQ_OK;
@@ -1638,6 +1849,9 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
         h->lam_f = fin.x;
         h->M = b->M[i];
         h->have_force = b->want_force && h->natom > 0;
+        h->q0 = 0;
+        h->q1 = h->N_d;
+        h->have_moments = 1;
         h->have_density = 1;
         if (lambda_f) lambda_f[i] = fin.x;
     }
@@ -1819,7 +2033,8 @@ extern "C" sq_status sq_density_vjp(sq_handle h, const double *d_rho_bar, double
 {
     g_last_error[0] = 0;
     if (!h || !d_rho_bar || !d_veff_bar) return fail(SQ_ERR_ARG, "null argument");
-    if (!h->have_density) return fail(SQ_ERR_STATE, "sq_density_vjp before sq_density");
+    if (!h->have_density || h->q0 != 0 || h->q1 != h->N_d)
+        return fail(SQ_ERR_STATE, "sq_density_vjp needs a whole-grid sq_density first");
     if (checkpoint_k < 1 || checkpoint_k > h->K) return fail(SQ_ERR_ARG, "checkpoint interval %d (K = %d)", checkpoint_k, h->K);
     if (!std::isfinite(U_bar)) return fail(SQ_ERR_NOT_FINITE, "U_bar");
     cudaStream_t stream = (cudaStream_t)stream_;

@@ -11,6 +11,9 @@ namespace sq {
 constexpr int kMaxHalfWidth = 8;   // FD order <= 16
 constexpr int kNumFactors = 4;     // g, hp (p factor), g', hp' per atom and axis
 
+// Adds n to the library's count of launched kernels (sq_kernel_launches).
+void count_launches(long long n);
+
 // Per-precision device data derived from the handle for one recursion launch.
 template <typename T>
 struct RecursionArgs {
@@ -19,6 +22,7 @@ struct RecursionArgs {
     int nc[3];           // cube extents 2m+1
     int nc3;             // cube points
     long long N_d;       // grid points
+    long long q0, q1;    // columns [q0, q1) of this launch (0 and N_d for the whole grid)
     int K;               // polynomial order
     int natom;
     int nproj;           // 1 (s) or 4 (s + p)

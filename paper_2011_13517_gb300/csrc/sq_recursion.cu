@@ -512,7 +512,7 @@ template <typename T, int P, int BLOCK, bool VSMEM>
 __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 2 : 1) recursion_kernel(const RecursionArgs<T> args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    column_range<T, P, BLOCK, VSMEM>(args, blockIdx.x, args.N_d, gridDim.x, smem_raw,
+    column_range<T, P, BLOCK, VSMEM>(args, args.q0 + blockIdx.x, args.q1, gridDim.x, smem_raw,
                                      VSMEM ? nullptr : args.scratch + (size_t)blockIdx.x * 2 * args.nc3);
 }
 
@@ -522,7 +522,7 @@ template <typename T, int P>
 __global__ void __launch_bounds__(256, 2) adjoint_kernel(const RecursionArgs<T> args, long long scratch_stride)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    column_range<T, P, 256, false, true>(args, blockIdx.x, args.N_d, gridDim.x, smem_raw,
+    column_range<T, P, 256, false, true>(args, args.q0 + blockIdx.x, args.q1, gridDim.x, smem_raw,
                                          args.scratch + (size_t)blockIdx.x * scratch_stride);
 }
 

@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_kernel(const RecursionArgs<fl
 
     for (int i = threadIdx.x; i < NZ / 2; i += NTH) S.zero[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    for (long long q = blockIdx.x; q < N_d; q += gridDim.x) {
+    for (long long q = args.q0 + blockIdx.x; q < args.q1; q += gridDim.x) {
         int qa[3], nfrc = 0;
         const int nact = slab_setup<NC>(args, S, q, amax, fmax, err, qa, &nfrc);
         if (nact < 0) continue;
@@ -761,7 +761,7 @@ __global__ void __launch_bounds__(NC * 32, 1) slab_adjoint_kernel(const Recursio
 
     for (int i = threadIdx.x; i < NZ / 2; i += NTH) S.zero[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    for (long long q = blockIdx.x; q < N_d; q += gridDim.x) {
+    for (long long q = args.q0 + blockIdx.x; q < args.q1; q += gridDim.x) {
         int qa[3], nfrc = 0;
         const int nact = slab_setup<NC>(args, S, q, amax, 1, err, qa, &nfrc);
         if (nact < 0) continue;

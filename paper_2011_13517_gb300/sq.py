@@ -24,11 +24,12 @@ STATUS = {0: "SQ_OK", 1: "SQ_ERR_ARG", 2: "SQ_ERR_CUBE_EXCEEDS_BOX", 3: "SQ_ERR_
           4: "SQ_ERR_NOT_FINITE", 5: "SQ_ERR_CUDA", 6: "SQ_ERR_TIMEOUT", 7: "SQ_ERR_OOM",
           8: "SQ_ERR_STATE", 9: "SQ_ERR_UNSUPPORTED"}
 
-EXPORTS = ["sq_build_hamiltonian", "sq_density", "sq_fermi_level", "sq_energy", "sq_nonlocal_force",
+EXPORTS = ["sq_build_hamiltonian", "sq_density", "sq_fermi_level", "sq_fermi_weights", "sq_fermi_resolve",
+           "sq_moments_range", "sq_observables", "sq_energy", "sq_nonlocal_force",
            "sq_get_spectral_bounds", "sq_get_moments", "sq_copy_moments", "sq_get_cube", "sq_get_timing",
-           "sq_kernel_launches", "sq_moments_noalloc", "sq_batch_create", "sq_batch_density", "sq_batch_info",
-           "sq_batch_destroy", "sq_density_vjp", "sq_kernel_name", "sq_destroy", "sq_status_string",
-           "sq_last_error"]
+           "sq_kernel_launches", "sq_fma_throughput", "sq_moments_noalloc", "sq_batch_create", "sq_batch_density",
+           "sq_batch_info", "sq_batch_destroy", "sq_density_vjp", "sq_kernel_name", "sq_destroy",
+           "sq_status_string", "sq_last_error"]
 
 
 class SQError(RuntimeError):
@@ -62,7 +63,14 @@ def lib():
                                            ctypes.c_double, ctypes.c_double, vp, ctypes.POINTER(vp)]
         L.sq_density.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                  vp, dp, vp]
-        L.sq_fermi_level.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, dp, vp]
+        d = ctypes.c_double
+        L.sq_fermi_level.argtypes = [dp, ctypes.c_int, d, d, d, d, d, d, dp]
+        L.sq_fermi_weights.argtypes = [d, ctypes.c_int, d, d, d, dp, dp, dp]
+        L.sq_fermi_resolve.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, dp, vp]
+        L.sq_moments_range.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                                       ctypes.c_longlong, dp, dp, vp]
+        L.sq_observables.argtypes = [vp, d, d, d, dp, dp, vp, vp]
+        L.sq_fma_throughput.argtypes = [ctypes.c_int, dp, dp, vp]
         L.sq_energy.argtypes = [vp, dp, dp, dp, vp]
         L.sq_nonlocal_force.argtypes = [vp, vp, vp]
         L.sq_get_spectral_bounds.argtypes = [vp, dp, dp]
@@ -106,17 +114,27 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _dev_ptr(t, dtype=torch.float64):
+def _dev_ptr(t, dtype=torch.float64, numel=None):
+    """Raw pointer of a contiguous CUDA tensor of the given dtype holding at least `numel` elements.
+    The library writes through these pointers without knowing the tensor's size, so a short buffer
+    is rejected here, before any launch."""
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"buffer holds {t.numel()} elements, the call writes {numel}")
     if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
         raise ValueError(f"expected a contiguous CUDA {dtype} tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
 class Handle:
-    """Owns an sq_handle and the host arrays its build call read."""
+    """Owns an sq_handle; remembers the sizes its outputs need (grid points, atoms, projectors)."""
 
-    def __init__(self, ptr):
+    def __init__(self, ptr, N_d=None, natom=None, nproj=None):
         self.ptr = ctypes.c_void_p(ptr)
+        self.N_d = N_d
+        self.natom = natom
+        self.nproj = nproj
+        self.K = None
+        self.range = None
 
     def __del__(self):
         self.close()
@@ -145,25 +163,88 @@ def sq_build_hamiltonian(n, L, fd_order, d_veff, R, lmax, sigma, rc, energy, R_c
     at.sigma = float(sigma)
     at.rc = float(rc)
     at.energy = en.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    N_d = int(g.n[0]) * int(g.n[1]) * int(g.n[2])
     out = ctypes.c_void_p()
-    _check(lib().sq_build_hamiltonian(ctypes.byref(g), _dev_ptr(d_veff), ctypes.byref(at), float(R_cut),
+    _check(lib().sq_build_hamiltonian(ctypes.byref(g), _dev_ptr(d_veff, numel=N_d), ctypes.byref(at), float(R_cut),
                                       float(lambda_min), float(lambda_max), _stream(stream), ctypes.byref(out)))
-    return Handle(out.value)
+    return Handle(out.value, N_d=N_d, natom=at.natom, nproj=1 if int(lmax) == 0 else 4)
 
 
 def sq_density(h: Handle, K, kT, N_e, precision, flags, d_rho, stream=None) -> float:
     lam = ctypes.c_double()
-    _check(lib().sq_density(h.ptr, int(K), float(kT), float(N_e), int(precision), int(flags), _dev_ptr(d_rho),
-                            ctypes.byref(lam), _stream(stream)))
+    _check(lib().sq_density(h.ptr, int(K), float(kT), float(N_e), int(precision), int(flags),
+                            _dev_ptr(d_rho, numel=h.N_d), ctypes.byref(lam), _stream(stream)))
+    h.K, h.range = int(K), (0, h.N_d)
     return lam.value
 
 
-def sq_fermi_level(h: Handle, kT, N_e, d_rho=None, stream=None) -> float:
+def sq_fermi_resolve(h: Handle, kT, N_e, d_rho=None, stream=None) -> float:
+    """Re-solve the Fermi level of the last whole-grid sq_density for another kT / N_e (device)."""
     lam = ctypes.c_double()
-    _check(lib().sq_fermi_level(h.ptr, float(kT), float(N_e),
-                                _dev_ptr(d_rho) if d_rho is not None else ctypes.c_void_p(None),
-                                ctypes.byref(lam), _stream(stream)))
+    _check(lib().sq_fermi_resolve(h.ptr, float(kT), float(N_e),
+                                  _dev_ptr(d_rho, numel=h.N_d) if d_rho is not None else ctypes.c_void_p(None),
+                                  ctypes.byref(lam), _stream(stream)))
     return lam.value
+
+
+def _host_f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if a.size < n:
+        raise ValueError(f"array holds {a.size} values, {n} are needed")
+    return a
+
+
+def sq_fermi_level(msum, K, omega, tau, lambda_min, lambda_max, kT, N_e) -> float:
+    """Pure host Fermi level from moment sums M_k (Eq. Ne); no handle, no GPU."""
+    m = _host_f64(msum, int(K) + 1)
+    lam = ctypes.c_double()
+    _check(lib().sq_fermi_level(m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(K), float(omega), float(tau),
+                                float(lambda_min), float(lambda_max), float(kT), float(N_e), ctypes.byref(lam)))
+    return lam.value
+
+
+def sq_fermi_weights(lambda_f, K, omega, tau, kT):
+    """Host Chebyshev weights (c, d, e) [K+1] of g, lam g and s(g) at lambda_f."""
+    out = [np.zeros(int(K) + 1) for _ in range(3)]
+    ptr = [o.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for o in out]
+    _check(lib().sq_fermi_weights(float(lambda_f), int(K), float(omega), float(tau), float(kT), *ptr))
+    return tuple(out)
+
+
+def sq_moments_range(h: Handle, K, precision, flags, q_begin, q_end, stream=None):
+    """Recursion over columns [q_begin, q_end): returns (partial M_k [K+1], partial force moments
+    [K+1, natom, nproj, 3] or None)."""
+    K = int(K)
+    msum = np.zeros(K + 1)
+    want_force = bool(int(flags) & SQ_WANT_FORCE) and h.natom
+    A = np.zeros((K + 1, h.natom, h.nproj, 3)) if want_force else None
+    _check(lib().sq_moments_range(h.ptr, K, int(precision), int(flags), int(q_begin), int(q_end),
+                                  msum.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  A.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if A is not None else None,
+                                  _stream(stream)))
+    h.K, h.range = K, (int(q_begin), int(q_end))
+    return msum, A
+
+
+def sq_observables(h: Handle, lambda_f, kT, N_e, msum, A=None, d_rho=None, stream=None):
+    """After sq_moments_range: total sums in, density of the range's columns out (d_rho [q_end - q_begin])."""
+    if h.K is None or h.range is None:
+        raise ValueError("sq_observables needs sq_moments_range first")
+    m = _host_f64(msum, h.K + 1)
+    Ah = _host_f64(A, (h.K + 1) * h.natom * h.nproj * 3) if A is not None else None
+    n = h.range[1] - h.range[0]
+    _check(lib().sq_observables(h.ptr, float(lambda_f), float(kT), float(N_e),
+                                m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                Ah.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if Ah is not None else None,
+                                _dev_ptr(d_rho, numel=n) if d_rho is not None else ctypes.c_void_p(None),
+                                _stream(stream)))
+
+
+def sq_fma_throughput(precision, stream=None):
+    """Measured FMA ceiling (TFLOP/s, ms of the timed probe launch) of the current GPU."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().sq_fma_throughput(int(precision), ctypes.byref(t), ctypes.byref(ms), _stream(stream)))
+    return t.value, ms.value
 
 
 def sq_energy(h: Handle, stream=None):
@@ -173,7 +254,7 @@ def sq_energy(h: Handle, stream=None):
 
 
 def sq_nonlocal_force(h: Handle, d_force, stream=None):
-    _check(lib().sq_nonlocal_force(h.ptr, _dev_ptr(d_force), _stream(stream)))
+    _check(lib().sq_nonlocal_force(h.ptr, _dev_ptr(d_force, numel=3 * h.natom), _stream(stream)))
 
 
 def sq_get_spectral_bounds(h: Handle):
@@ -197,8 +278,8 @@ def sq_get_timing(h: Handle):
 
 def sq_density_vjp(h: Handle, d_rho_bar, U_bar, checkpoint_k, d_veff_bar, stream=None):
     """sq_density_vjp: d_veff_bar = dL/dV_eff for L = sum rho_bar rho + U_bar U (see include/sq.h)."""
-    _check(lib().sq_density_vjp(h.ptr, _dev_ptr(d_rho_bar), float(U_bar), int(checkpoint_k), _dev_ptr(d_veff_bar),
-                                _stream(stream)))
+    _check(lib().sq_density_vjp(h.ptr, _dev_ptr(d_rho_bar, numel=h.N_d), float(U_bar), int(checkpoint_k),
+                                _dev_ptr(d_veff_bar, numel=h.N_d), _stream(stream)))
 
 
 def sq_kernel_name(h: Handle) -> str:
@@ -214,7 +295,8 @@ def sq_moments_noalloc(h: Handle, K, precision, d_mu, stream=None):
     for SQ_FP32) with no device allocation by the library; see include/sq.h for the shared fixed
     scratch array and its rules."""
     dt = torch.float64 if precision == SQ_FP64 else torch.float32
-    _check(lib().sq_moments_noalloc(h.ptr, int(K), int(precision), _dev_ptr(d_mu, dt), _stream(stream)))
+    _check(lib().sq_moments_noalloc(h.ptr, int(K), int(precision), _dev_ptr(d_mu, dt, numel=(int(K) + 1) * h.N_d),
+                                    _stream(stream)))
 
 
 class Batch:
@@ -248,7 +330,7 @@ def sq_batch_create(handles, K, kT, N_e, precision, flags) -> Batch:
 
 def sq_batch_density(b: Batch, d_rhos, stream=None):
     n = len(b.handles)
-    ptrs = (ctypes.c_void_p * n)(*[_dev_ptr(r).value for r in d_rhos])
+    ptrs = (ctypes.c_void_p * n)(*[_dev_ptr(r, numel=h.N_d).value for r, h in zip(d_rhos, b.handles)])
     lam = np.zeros(n)
     _check(lib().sq_batch_density(b.ptr, ptrs, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
     return lam

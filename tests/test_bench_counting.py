@@ -27,3 +27,37 @@ def test_flop_count_without_atoms_is_the_stencil_count():
 def test_vacancy_flop_count():
     """24.968 TFLOP per launch on the vacancy cell (the figure the bench's roofline divides)."""
     assert abs(bench.algorithmic_flops(cells.vacancy_cell()) / 1e12 - 24.96816041472) < 1e-9
+
+
+def test_ball_count_matches_periodic_convolution():
+    """The ball-support FLOP count (sum_q |B ^ C_q| = |B| n_c^3, and the force term as the ball's
+    autocorrelation over the cube offsets) against a direct periodic convolution on the full grid:
+    for every column q, |B ^ C_q| = (1_B * 1_C)(q), summed over all q, and over q inside B."""
+    c = cells.vacancy_cell()
+    nz, ny, nx = int(c.n[2]), int(c.n[1]), int(c.n[0])
+    m = c.m
+    cube = np.zeros((nz, ny, nx))
+    for dz in range(-m[2], m[2] + 1):
+        for dy in range(-m[1], m[1] + 1):
+            cube[dz % nz, dy % ny, (np.arange(-m[0], m[0] + 1)) % nx] = 1.0
+    Fc = np.fft.fftn(cube)
+    for J in (0, 17, 94):
+        x = [np.arange(int(c.n[a])) * c.h[a] - c.R[J, a] for a in range(3)]
+        d = [xa - c.box[a] * np.round(xa / c.box[a]) for a, xa in enumerate(x)]
+        ball = (d[2][:, None, None] ** 2 + d[1][None, :, None] ** 2 + d[0][None, None, :] ** 2) < c.proj_rc ** 2
+        per_q = np.rint(np.real(np.fft.ifftn(np.fft.fftn(ball.astype(float)) * Fc)))
+        b = bench.ball_support(c, J)
+        assert int(ball.sum()) == int(b.sum())
+        from scipy.signal import fftconvolve
+        ac = fftconvolve(b.astype(float), b[::-1, ::-1, ::-1].astype(float))
+        cz, cy, cx = np.array(b.shape) - 1
+        force = np.rint(ac[cz - m[2]:cz + m[2] + 1, cy - m[1]:cy + m[1] + 1, cx - m[0]:cx + m[0] + 1].sum())
+        assert int(per_q.sum()) == int(ball.sum()) * int(np.prod(c.n_c))
+        assert int(per_q[ball].sum()) == int(force)
+
+
+def test_ball_count_without_atoms_is_the_stencil_count():
+    c = cells.tiny_cell()
+    c.R = c.R[:0]
+    nc3 = int(np.prod(c.n_c))
+    assert bench.algorithmic_flops_ball(c) == 2.0 * c.N_d * c.K * nc3 * (3 * c.fd_order + 2)

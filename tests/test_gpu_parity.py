@@ -225,6 +225,29 @@ def test_precision_cell_fp32_against_oracle_golden():
     assert e["dlam"] < 1e-5 and e["dU_atom"] < 1e-4 and e["rho_rel"] < 1e-4 and e["df"] < 1e-4
 
 
+def test_precision_cell_fp64_against_oracle_golden():
+    """FP64 recursion on the 286-atom divacancy + Al cell (73x63x79 grid, 29^3 cubes, K = 80) against
+    the FP64 oracle's full-size golden values: lambda_f within 1e-12, U and S within 1e-10 relative,
+    rho within 1e-10 relative at the 2,050 golden points, forces within 1e-9 of the largest component,
+    and all K+1 moments of the 34 golden columns within 1e-12."""
+    path = os.path.join(GOLDEN, "precision_286atom.json")
+    if not os.path.exists(path):
+        pytest.skip("golden file not generated")
+    g = json.load(open(path))
+    c = cells.precision_cell()
+    assert c.digest() == g["digest"]
+    gpu = sq.solve_cell(c, sq.SQ_FP64, force=True, bounds=(g["lmin"], g["lmax"]))
+    assert abs(gpu["lam_f"] - g["lam_f"]) < 1e-12
+    assert rel(gpu["U"], g["U"]) < 1e-10 and rel(gpu["S"], g["S"]) < 1e-10
+    np.testing.assert_allclose(gpu["Msum"], g["Msum"], rtol=1e-11, atol=1e-11 * c.N_d)
+    idx = np.array(g["rho_idx"])
+    gr = np.array(g["rho"])
+    np.testing.assert_allclose(gpu["rho"][idx], gr, rtol=1e-10, atol=1e-10 * np.abs(gr).max())
+    gf = np.array(g["force"])
+    np.testing.assert_allclose(gpu["force"], gf, rtol=0, atol=1e-9 * np.abs(gf).max())
+    np.testing.assert_allclose(gpu["mu"][:, np.array(g["mu_idx"])].T, np.array(g["mu"]), rtol=0, atol=1e-12)
+
+
 def test_fp32_21_cube_matches_oracle():
     """FP32 on a 21^3 cube (R_cut = 5 bohr, the batch workload's smallest truncation): sampled
     moments of a 48-site cell against the oracle."""
@@ -273,7 +296,7 @@ def test_bad_arguments_and_state():
     # with kT far above the band width g is ~1/2 on the whole spectrum, so N(lambda_max) ~ N_d and
     # an electron count of 1.5 N_d cannot be bracketed
     with pytest.raises(sq.SQError) as ei:
-        sq.sq_fermi_level(h, 1e4, 1.5 * c.N_d)
+        sq.sq_fermi_resolve(h, 1e4, 1.5 * c.N_d)
     assert ei.value.status == 3
     h.close()
 
@@ -288,12 +311,12 @@ def test_non_finite_potential_is_rejected():
 
 
 def test_fermi_level_resolve_matches_oracle(tiny):
-    """sq_fermi_level re-solves Eq. Ne for another electron count from the stored moment sums."""
+    """sq_fermi_resolve re-solves Eq. Ne for another electron count from the stored moment sums."""
     c, ref = tiny
     h = sq.build_for_cell(c, bounds=(ref["lmin"], ref["lmax"]))
     rho = torch.empty(c.N_d, dtype=torch.float64, device="cuda")
     sq.sq_density(h, c.K, c.kT, c.N_e, sq.SQ_FP64, 0, rho)
-    lam2 = sq.sq_fermi_level(h, 0.02, 20.0, rho)
+    lam2 = sq.sq_fermi_resolve(h, 0.02, 20.0, rho)
     exp = oracle.fermi_level(ref["Msum"], ref["omega"], ref["tau"], 0.02, 20.0, ref["lmin"], ref["lmax"],
                              oracle.n_nodes(c.K, 0.02, ref["tau"]))
     assert abs(lam2 - exp) < 1e-12

@@ -1,0 +1,82 @@
+"""CPU checks of the library's host-side logic (no GPU needed):
+
+- the pure host Fermi level (sq_fermi_level, Eq. Ne) and Chebyshev weights (sq_fermi_weights,
+  Eq. ChebyshevWeights) against the oracle on the same moment sums;
+- their error paths (no bracket, bad arguments);
+- the binding's buffer-size checks, which run before anything reaches the library."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2011_13517_gb300 import cells, sq
+
+
+@pytest.fixture(scope="module")
+def tiny_ref():
+    c = cells.tiny_cell()
+    return c, oracle.sq_solve(c, force=False)
+
+
+def test_host_fermi_level_matches_oracle(tiny_ref):
+    c, ref = tiny_ref
+    lam = sq.sq_fermi_level(ref["Msum"], c.K, ref["omega"], ref["tau"], ref["lmin"], ref["lmax"], c.kT, c.N_e)
+    assert abs(lam - ref["lam_f"]) < 1e-12
+    # another smearing and electron count on the same sums
+    M = oracle.n_nodes(c.K, 0.02, ref["tau"])
+    exp = oracle.fermi_level(ref["Msum"], ref["omega"], ref["tau"], 0.02, 20.0, ref["lmin"], ref["lmax"], M)
+    lam2 = sq.sq_fermi_level(ref["Msum"], c.K, ref["omega"], ref["tau"], ref["lmin"], ref["lmax"], 0.02, 20.0)
+    assert abs(lam2 - exp) < 1e-12
+
+
+def test_host_weights_match_oracle_and_give_the_observables(tiny_ref):
+    c, ref = tiny_ref
+    M = oracle.n_nodes(c.K, c.kT, ref["tau"])
+    cw, dw, ew = sq.sq_fermi_weights(ref["lam_f"], c.K, ref["omega"], ref["tau"], c.kT)
+    oc, od, oe = oracle.fermi_coeffs(ref["lam_f"], ref["omega"], ref["tau"], c.kT, c.K, M)
+    np.testing.assert_allclose(cw, oc, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(dw, od, rtol=0, atol=1e-13 * max(1.0, np.abs(od).max()))
+    np.testing.assert_allclose(ew, oe, rtol=0, atol=1e-13)
+    assert abs(2.0 * dw @ ref["Msum"] - ref["U"]) < 1e-10 * abs(ref["U"])
+    assert abs(-2.0 * ew @ ref["Msum"] - ref["S"]) < 1e-10 * abs(ref["S"])
+    rho = 2.0 * (ref["mu"] @ cw) / ref["dV"]
+    np.testing.assert_allclose(rho, ref["rho"], rtol=1e-11, atol=1e-13)
+
+
+def test_host_fermi_full_band_weights():
+    """lambda_f far above the spectrum: g = 1 on [-1, 1], so c_0 = 1 and c_k = 0 for k > 0."""
+    c, _, _ = sq.sq_fermi_weights(1e3, 12, 0.0, 1.0, 0.01)
+    assert abs(c[0] - 1.0) < 1e-14 and np.max(np.abs(c[1:])) < 1e-14
+
+
+def test_host_fermi_errors(tiny_ref):
+    c, ref = tiny_ref
+    with pytest.raises(sq.SQError) as ei:   # more electrons than the band holds
+        sq.sq_fermi_level(ref["Msum"], c.K, ref["omega"], ref["tau"], ref["lmin"], ref["lmax"], c.kT, 2.5 * c.N_d)
+    assert ei.value.status == 3
+    with pytest.raises(sq.SQError) as ei:
+        sq.sq_fermi_level(ref["Msum"], c.K, ref["omega"], ref["tau"], ref["lmax"], ref["lmin"], c.kT, c.N_e)
+    assert ei.value.status == 1
+    bad = ref["Msum"].copy()
+    bad[3] = math.nan
+    with pytest.raises(sq.SQError) as ei:
+        sq.sq_fermi_level(bad, c.K, ref["omega"], ref["tau"], ref["lmin"], ref["lmax"], c.kT, c.N_e)
+    assert ei.value.status == 4
+    with pytest.raises(ValueError):
+        sq.sq_fermi_level(ref["Msum"][:5], c.K, ref["omega"], ref["tau"], ref["lmin"], ref["lmax"], c.kT, c.N_e)
+
+
+def test_binding_rejects_short_output_buffers():
+    """The library writes (K+1) N_d moments, N_d densities or 3 natom forces through raw pointers; a
+    shorter tensor must be refused before any launch."""
+    torch = pytest.importorskip("torch")
+    h = sq.Handle(None, N_d=100, natom=4, nproj=4)
+    with pytest.raises(ValueError, match="elements"):
+        sq.sq_moments_noalloc(h, 3, sq.SQ_FP64, torch.zeros(399, dtype=torch.float64))
+    with pytest.raises(ValueError, match="elements"):
+        sq.sq_density(h, 3, 0.01, 8.0, sq.SQ_FP64, 0, torch.zeros(99, dtype=torch.float64))
+    with pytest.raises(ValueError, match="elements"):
+        sq.sq_nonlocal_force(h, torch.zeros(11, dtype=torch.float64))
+    with pytest.raises(ValueError, match="elements"):
+        sq.sq_density_vjp(h, torch.zeros(50, dtype=torch.float64), 0.0, 1, torch.zeros(100, dtype=torch.float64))

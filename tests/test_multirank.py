@@ -3,7 +3,10 @@
 Columns are independent given V_eff (Sec. 3, "Spectral weights, nodes and electronic fields"), so
 ranks take disjoint column ranges and need one collective: a sum of the K+1 moment sums before the
 Fermi solve (the paper's single global reduction, Eq. Ne).  Each rank then forms its own part of
-rho.  The result must equal the single-process solve."""
+rho.  On the CPU the per-column moments come from the oracle (the library's recursion needs a GPU);
+the Fermi level and the weights after the allreduce come from the library's pure host entry points
+sq_fermi_level and sq_fermi_weights, the calls a sharded GPU run makes.  The result must equal the
+single-process oracle solve."""
 import os
 import socket
 
@@ -33,15 +36,16 @@ def _worker(rank, world, port, out_path):
     mu = oracle.moments(c, omega, tau, cols=cols, nthreads=2)
     msum = torch.from_numpy(mu.sum(axis=0))
     dist.all_reduce(msum, op=dist.ReduceOp.SUM)
-    M = oracle.n_nodes(c.K, c.kT, tau)
-    lam_f = oracle.fermi_level(msum.numpy(), omega, tau, c.kT, c.N_e, lo, hi, M)
-    coef, _, _ = oracle.fermi_coeffs(lam_f, omega, tau, c.kT, c.K, M)
-    rho_part = torch.from_numpy(oracle.density(mu, coef, float(np.prod(c.h))))
+    from paper_2011_13517_gb300 import sq
+    lam_f = sq.sq_fermi_level(msum.numpy(), c.K, omega, tau, lo, hi, c.kT, c.N_e)
+    coef, dcoef, _ = sq.sq_fermi_weights(lam_f, c.K, omega, tau, c.kT)
+    rho_part = torch.from_numpy(2.0 * (mu @ coef) / float(np.prod(c.h)))
+    U = 2.0 * float(dcoef @ msum.numpy())
     # gather the density parts (equal-sized shards here: 3570 = 2 x 1785)
     parts = [torch.zeros_like(rho_part) for _ in range(world)]
     dist.all_gather(parts, rho_part)
     if rank == 0:
-        np.savez(out_path, lam_f=lam_f, msum=msum.numpy(), rho=torch.cat(parts).numpy())
+        np.savez(out_path, lam_f=lam_f, msum=msum.numpy(), rho=torch.cat(parts).numpy(), U=U)
     dist.barrier()
     dist.destroy_process_group()
 
@@ -58,3 +62,4 @@ def test_two_rank_column_shard_matches_single_process(tmp_path):
     assert abs(float(got["lam_f"]) - ref["lam_f"]) < 1e-12
     np.testing.assert_allclose(got["msum"], ref["Msum"], rtol=1e-13, atol=1e-12)
     np.testing.assert_allclose(got["rho"], ref["rho"], rtol=1e-12, atol=1e-14)
+    assert abs(float(got["U"]) - ref["U"]) < 1e-11 * abs(ref["U"])
