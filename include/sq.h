@@ -54,6 +54,14 @@ enum { SQ_FP64 = 0, SQ_FP32 = 1 };
 /* flags of sq_density */
 enum { SQ_WANT_FORCE = 1 };
 
+/* flags of sq_build_hamiltonian: the gradient of the projectors in the nonlocal force.
+ * SQ_GRAD_ANALYTIC: the analytic gradient of chi.
+ * SQ_GRAD_FD: the paper's discrete form (Sec. 3 "Atomic forces"), the central finite-difference
+ *   gradient nabla_h of the same order as the Laplacian; the paper applies it to the density
+ *   matrix columns, f_J = -4 sum_q e_q^T V_J nabla_h(gamma e_q), which on the periodic grid equals
+ *   the same contraction with nabla_h chi in place of the analytic gradient (nabla_h^T = -nabla_h). */
+enum { SQ_GRAD_ANALYTIC = 0, SQ_GRAD_FD = 1 };
+
 /* Regular periodic grid (Sec. 3 "Discretization"): n_i points on [0, L_i), h_i = L_i / n_i, and the
  * central finite-difference Laplacian of even order fd_order = n_o in {2, 4, ..., 16}. */
 typedef struct {
@@ -91,6 +99,7 @@ typedef struct {
  *   R_cut       half-width of the truncation cube (bohr); cube half-widths m_i = round(R_cut/h_i)
  *               (ties to even).  Requires 2 m_i + 1 + fd_order/2 <= n_i on every axis, so that no
  *               two cube points are stencil neighbours through the periodic wrap.
+ *   flags       SQ_GRAD_ANALYTIC or SQ_GRAD_FD (gradient used by the force moments)
  *   lambda_min, lambda_max
  *               spectral bounds of H used for the scale and shift omega = (max+min)/2,
  *               tau = (max-min)/2.  Pass NaN for both to let the library compute the rigorous bound
@@ -103,7 +112,7 @@ typedef struct {
  * SQ_ERR_CUDA.  Synchronises `stream`.
  */
 sq_status sq_build_hamiltonian(const sq_grid *grid, const double *d_veff, const sq_atoms *atoms,
-                               double R_cut, double lambda_min, double lambda_max, void *stream,
+                               double R_cut, int flags, double lambda_min, double lambda_max, void *stream,
                                sq_handle *out);
 
 /*

@@ -53,6 +53,7 @@ class _Problem(ctypes.Structure):
         ("cl", ctypes.POINTER(ctypes.c_double)),
         ("m", ctypes.c_int * 3),
         ("full", ctypes.c_int),
+        ("grad_fd", ctypes.c_int),
     ]
 
 
@@ -63,6 +64,7 @@ def lib():
         dp = ctypes.POINTER(ctypes.c_double)
         lp = ctypes.POINTER(ctypes.c_long)
         _lib.sq_oracle_fd_coeffs.argtypes = [ctypes.c_int, dp]
+        _lib.sq_oracle_fd1_coeffs.argtypes = [ctypes.c_int, dp]
         _lib.sq_oracle_axis_factors.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                 ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
         _lib.sq_oracle_apply.argtypes = [ctypes.POINTER(_Problem), ctypes.c_long, ctypes.c_double,
@@ -87,7 +89,7 @@ def _lp(a):
 class Problem:
     """ctypes view of a Cell (keeps the arrays alive)."""
 
-    def __init__(self, cell, full: bool = False, m=None):
+    def __init__(self, cell, full: bool = False, m=None, grad_fd: bool = False):
         self.cell = cell
         self.veff = np.ascontiguousarray(cell.veff, dtype=np.float64)
         self.R = np.ascontiguousarray(cell.R, dtype=np.float64).reshape(-1)
@@ -106,6 +108,7 @@ class Problem:
         st.rc = float(cell.proj_rc)
         st.cl = _dp(self.cl)
         st.full = 1 if full else 0
+        st.grad_fd = 1 if grad_fd else 0
         self.st = st
         self.full = full
         self.nc = cell.n.copy() if full else 2 * np.array([st.m[0], st.m[1], st.m[2]]) + 1
@@ -121,6 +124,16 @@ def fd_coeffs(order: int) -> np.ndarray:
     if p < 0:
         raise ValueError("bad FD order")
     return c[: p + 1].copy()
+
+
+def fd1_coeffs(order: int) -> np.ndarray:
+    """Central 1st-derivative FD weights a_0..a_p (a_0 = 0) of the gradient nabla_h (Sec. 3, local and
+    nonlocal forces; same order as the Laplacian)."""
+    a = np.zeros(17)
+    p = lib().sq_oracle_fd1_coeffs(order, _dp(a))
+    if p < 0:
+        raise ValueError("bad FD order")
+    return a[: p + 1].copy()
 
 
 def axis_factors(R_a, L_a, n_a, sigma, rc):
@@ -238,12 +251,12 @@ def cube_indices(cell, q, full=False, m=None):
     return out
 
 
-def moments(cell, omega, tau, K=None, cols=None, force=False, nthreads=0, full=False, m=None):
+def moments(cell, omega, tau, K=None, cols=None, force=False, nthreads=0, full=False, m=None, grad_fd=False):
     """mu [ncols, K+1] with mu_k^q = (T_k(Hhat_q))_qq, and (if force) the force moments
-    A [K+1, natom, nproj, 3] summed over the given columns."""
+    A [K+1, natom, nproj, 3] summed over the given columns (grad_fd: with the FD gradient D_h chi)."""
     K = cell.K if K is None else K
     cols = np.arange(cell.N_d, dtype=np.int64) if cols is None else np.ascontiguousarray(cols, dtype=np.int64)
-    prob = Problem(cell, full=full, m=m)
+    prob = Problem(cell, full=full, m=m, grad_fd=grad_fd)
     mu = np.zeros((cols.size, K + 1))
     nproj = 1 if cell.lmax == 0 else 4
     A = np.zeros((K + 1, cell.natom, nproj, 3)) if force else None
@@ -366,7 +379,7 @@ def nonlocal_force(A, c, cl, dV):
     return 4.0 * dV * np.einsum("k,kJld,l->Jd", c, A, cl_lm)
 
 
-def sq_solve(cell, force=True, bounds=None, nthreads=0, full=False, K=None, cols_mu=None):
+def sq_solve(cell, force=True, bounds=None, nthreads=0, full=False, K=None, cols_mu=None, grad_fd=False):
     """The whole SQ evaluation for one cell, oracle side.  Returns a dict with the spectral bounds,
     omega, tau, M, moment sums, Fermi level, density rho (per bohr^3), U, S, F_band = U - kT S and
     the nonlocal forces [natom, 3]."""
@@ -375,7 +388,7 @@ def sq_solve(cell, force=True, bounds=None, nthreads=0, full=False, K=None, cols
     omega, tau = scale_shift(lmin, lmax)
     M = n_nodes(K, cell.kT, tau)
     dV = float(np.prod(cell.box / cell.n))
-    res = moments(cell, omega, tau, K=K, force=force, nthreads=nthreads, full=full)
+    res = moments(cell, omega, tau, K=K, force=force, nthreads=nthreads, full=full, grad_fd=grad_fd)
     mu, A = res if force else (res, None)
     Msum = mu.sum(axis=0)
     lam_f = fermi_level(Msum, omega, tau, cell.kT, cell.N_e, lmin, lmax, M)

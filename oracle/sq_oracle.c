@@ -24,7 +24,11 @@
  *  - the recursion starts from the Euclidean unit vector e_q, so mu_0 = 1;
  *  - the discrete KB term carries dV, because chi^T v approximates the integral of chi f;
  *  - projectors are separable windowed Gaussians (below), summed over periodic images;
- *  - the gradient in the force is the analytic gradient of chi.
+ *  - the gradient in the force is the analytic gradient of chi; with grad_fd set it is instead
+ *    the central finite-difference gradient D_h chi of the same order n_o as the Laplacian, the
+ *    discrete form of Sec. 3 "Atomic forces" (the paper applies nabla_h to gamma e_q; on the
+ *    periodic grid chi^T D_h v = -(D_h chi)^T v, so the force keeps its form with D_h chi in place
+ *    of the analytic gradient).
  *
  * Projectors.  With w(t) = exp(-t^2/(2 sigma^2)) (1 - t^2/rc^2)^3 for |t| < rc (0 otherwise),
  *   chi_s(x)   = N gx(x1-R1) gy(x2-R2) gz(x3-R3),          N = (pi sigma^2)^(-3/4),
@@ -50,6 +54,7 @@ typedef struct {
     const double *cl;      /* [lmax+1] KB energies */
     int m[3];              /* cube half-widths (grid points) */
     int full;              /* 1: no truncation, the "cube" is the whole periodic box */
+    int grad_fd;           /* 1: force moments with the FD gradient D_h chi instead of the analytic one */
 } sq_oracle_problem;
 
 enum { F_G = 0, F_HP = 1, F_GD = 2, F_HD = 3, NFACT = 4 };
@@ -71,6 +76,22 @@ int sq_oracle_fd_coeffs(int order, double *c)
         sum += c[j];
     }
     c[0] = -2.0 * sum;
+    return p;
+}
+
+/* Central first-derivative weights a_1..a_p of order n_o = 2p (df/dx ~ sum_j a_j (f_{+j} - f_{-j})/h):
+ *   a_j = (-1)^(j+1) (p!)^2 / (j (p-j)! (p+j)!).
+ * (Textbook Fornberg weights, the first-derivative companion of the Laplacian's.) */
+int sq_oracle_fd1_coeffs(int order, double *a)
+{
+    if (order < 2 || order % 2 || order > 32) return -1;
+    int p = order / 2;
+    a[0] = 0.0;
+    for (int j = 1; j <= p; j++) {
+        double r = 1.0;
+        for (int i = 1; i <= j; i++) r *= (double)(p - j + i) / (double)(p + i);
+        a[j] = ((j % 2) ? 1.0 : -1.0) * r / (double)j;
+    }
     return p;
 }
 
@@ -178,6 +199,23 @@ static int ctx_init(oracle_ctx *C, const sq_oracle_problem *P)
             sq_oracle_axis_factors(P->R[3 * J + a], P->L[a], na, P->sigma, P->rc,
                                    base + F_G * na, base + F_HP * na, base + F_GD * na,
                                    base + F_HD * na);
+            if (P->grad_fd) {
+                /* D_h of the separable factors: chi's FD gradient along axis a differentiates only
+                 * its axis-a factor, periodically on the n_a points */
+                double a1[17];
+                int p1 = sq_oracle_fd1_coeffs(P->fd_order, a1);
+                double h = P->L[a] / na;
+                for (int i = 0; i < na; i++) {
+                    double sg = 0.0, sh = 0.0;
+                    for (int j = 1; j <= p1; j++) {
+                        int ip = (i + j) % na, im = ((i - j) % na + na) % na;
+                        sg += a1[j] * (base[F_G * na + ip] - base[F_G * na + im]);
+                        sh += a1[j] * (base[F_HP * na + ip] - base[F_HP * na + im]);
+                    }
+                    base[F_GD * na + i] = sg / h;
+                    base[F_HD * na + i] = sh / h;
+                }
+            }
         }
     }
     return 0;
@@ -211,11 +249,16 @@ static inline int glob(const oracle_ctx *C, int a, int qa, int i)
     return g < 0 ? g + n : g;
 }
 
-/* Per-column list of the local indices where an atom's axis factor is nonzero. */
+/* Per-column list of the local indices where an atom's axis factor is nonzero, and the list the
+ * force moments contract over (the same, or with grad_fd the indices within p points of the
+ * support, where D_h g can be nonzero). */
 typedef struct {
     int cnt[3];
     int *idx[3];           /* local indices */
     int *gi[3];            /* matching global indices */
+    int cntd[3];
+    int *idxd[3];
+    int *gid[3];
 } atom_window;
 
 typedef struct {
@@ -228,7 +271,7 @@ typedef struct {
 static int column_atoms_build(const oracle_ctx *C, const int q3[3], column_atoms *ca)
 {
     const sq_oracle_problem *P = C->P;
-    int per = 2 * (C->nc[0] + C->nc[1] + C->nc[2]);
+    int per = 4 * (C->nc[0] + C->nc[1] + C->nc[2]);
     ca->atom = (int *)malloc(sizeof(int) * (P->natom > 0 ? P->natom : 1));
     ca->win = (atom_window *)malloc(sizeof(atom_window) * (P->natom > 0 ? P->natom : 1));
     ca->store = (int *)malloc(sizeof(int) * (size_t)per * (P->natom > 0 ? P->natom : 1));
@@ -254,6 +297,25 @@ static int column_atoms_build(const oracle_ctx *C, const int q3[3], column_atoms
                 }
             }
             if (wv->cnt[a] == 0) ok = 0;
+            wv->idxd[a] = s;
+            s += C->nc[a];
+            wv->gid[a] = s;
+            s += C->nc[a];
+            wv->cntd[a] = 0;
+            int reach = P->grad_fd ? C->p : 0;
+            for (int i = 0; i < C->nc[a]; i++) {
+                int gi = glob(C, a, q3[a], i);
+                int near = 0;
+                for (int j = -reach; j <= reach && !near; j++) {
+                    int gj = ((gi + j) % P->n[a] + P->n[a]) % P->n[a];
+                    near = g[gj] != 0.0;
+                }
+                if (near) {
+                    wv->idxd[a][wv->cntd[a]] = i;
+                    wv->gid[a][wv->cntd[a]] = gi;
+                    wv->cntd[a]++;
+                }
+            }
         }
         if (ok) ca->atom[ca->nact++] = J;
     }
@@ -463,11 +525,11 @@ int sq_oracle_moments(const sq_oracle_problem *P, double omega, double tau, int 
                                     const double *fy = factor(&C, J, 1, td[1]);
                                     const double *fz = factor(&C, J, 2, td[2]);
                                     double dot = 0.0;
-                                    for (int kc = 0; kc < wv->cnt[2]; kc++)
-                                        for (int kb = 0; kb < wv->cnt[1]; kb++)
-                                            for (int ka = 0; ka < wv->cnt[0]; ka++) {
-                                                long lc = wv->idx[0][ka] + (long)C.nc[0] * (wv->idx[1][kb] + (long)C.nc[1] * wv->idx[2][kc]);
-                                                dot += C.N * fx[wv->gi[0][ka]] * fy[wv->gi[1][kb]] * fz[wv->gi[2][kc]] * vcur[lc];
+                                    for (int kc = 0; kc < wv->cntd[2]; kc++)
+                                        for (int kb = 0; kb < wv->cntd[1]; kb++)
+                                            for (int ka = 0; ka < wv->cntd[0]; ka++) {
+                                                long lc = wv->idxd[0][ka] + (long)C.nc[0] * (wv->idxd[1][kb] + (long)C.nc[1] * wv->idxd[2][kc]);
+                                                dot += C.N * fx[wv->gid[0][ka]] * fy[wv->gid[1][kb]] * fz[wv->gid[2][kc]] * vcur[lc];
                                             }
                                     Aloc[(((long)k * P->natom + J) * nproj + lm) * 3 + d] += chi_q * dot;
                                 }

@@ -109,7 +109,7 @@ struct sq_handle_s {
     void *d_scratch = nullptr;      // per-CTA vectors when not in shared memory
     size_t scratch_cap = 0;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    int kernel_used = 0;            // 0: generic recursion kernel, 1: FP32 slab kernel
+    int kernel_used = 0;            // 0: generic recursion kernel, 1: FP32 slab kernel, 2: FP32 cluster kernel
     float t_rec = 0, t_msum = 0, t_fermi = 0;
 };
 
@@ -176,8 +176,45 @@ __global__ void k_factors(int natom, const double *R, double L0, double L1, doub
 }
 
 // Support (periodic interval where g != 0) of atom J on axis a: start and length.
+// Central first-derivative weights a_1..a_p of order 2p (host side, closed form).
+struct Fd1Weights {
+    double a[kMaxHalfWidth + 1];
+    int p;
+};
+
+// SQ_GRAD_FD: the derivative factors g', hp' of every atom and axis replaced by the periodic central
+// first difference of g, hp (order 2p, the order of the Laplacian), so the force moments contract
+// D_h chi instead of the analytic gradient (Sec. 3 "Atomic forces", discrete nonlocal force).
+__global__ void k_fd_gradient(int natom, double *fac64, int stride, int off0, int off1, int off2, int n0, int n1,
+                              int n2, double h0, double h1, double h2, Fd1Weights wt)
+{
+    const long long per_atom = (long long)n0 + n1 + n2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < natom * per_atom;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int J = (int)(t / per_atom);
+        int r = (int)(t % per_atom);
+        int ax = 0;
+        if (r >= n0) { r -= n0; ax = 1; }
+        if (ax == 1 && r >= n1) { r -= n1; ax = 2; }
+        const int n = ax == 0 ? n0 : (ax == 1 ? n1 : n2);
+        const double h = ax == 0 ? h0 : (ax == 1 ? h1 : h2);
+        double *base = fac64 + (size_t)J * stride + (ax == 0 ? off0 : (ax == 1 ? off1 : off2));
+        double sg = 0.0, sh = 0.0;
+        for (int j = 1; j <= wt.p; j++) {
+            const int ip = (r + j) % n, im = ((r - j) % n + n) % n;
+            sg += wt.a[j] * (base[ip] - base[im]);
+            sh += wt.a[j] * (base[n + ip] - base[n + im]);
+        }
+        base[2 * n + r] = sg / h;
+        base[3 * n + r] = sh / h;
+    }
+}
+
+// Support interval of every atom's factor g along each axis (start, length); with widen > 0 the
+// interval is extended by widen points on both sides (the reach of the FD gradient of SQ_GRAD_FD,
+// whose derivative tables are nonzero up to p points outside the support of g).
 __global__ void k_support(int natom, const double *fac64, int stride, int off0, int off1, int off2, int n0,
-                          int n1, int n2, int *sup, int *bad)
+                          int n1, int n2, int *sup, int *bad, int widen)
 {
     const int n[3] = {n0, n1, n2};
     const int off[3] = {off0, off1, off2};
@@ -196,6 +233,11 @@ __global__ void k_support(int natom, const double *fac64, int stride, int off0, 
         }
         if (cnt == n[a]) st = 0;
         else if (starts != 1) atomicExch(bad, 1);
+        if (widen > 0 && cnt < n[a]) {
+            st = ((st - widen) % n[a] + n[a]) % n[a];
+            cnt = cnt + 2 * widen < n[a] ? cnt + 2 * widen : n[a];
+            if (cnt == n[a]) st = 0;
+        }
         sup[J * 3 + a] = st;
         sup[natom * 3 + J * 3 + a] = cnt;
     }
@@ -525,6 +567,20 @@ static void fd_coefficients(int order, double *c)
     c[0] = -2.0 * sum;
 }
 
+static Fd1Weights fd1_coefficients(int order)
+{
+    // central first-derivative weights: a_j = (-1)^(j+1) (p!)^2 / (j (p-j)! (p+j)!)
+    Fd1Weights w;
+    memset(&w, 0, sizeof(w));
+    w.p = order / 2;
+    for (int j = 1; j <= w.p; j++) {
+        double r = 1.0;
+        for (int i = 1; i <= j; i++) r *= (double)(w.p - j + i) / (double)(w.p + i);
+        w.a[j] = ((j % 2) ? 1.0 : -1.0) * r / (double)j;
+    }
+    return w;
+}
+
 static double kinetic_max(const sq_handle_s *h)
 {
     // eigenvalues of -1/2 Lap_h on the periodic grid: sum_i -(c_0 + 2 sum_j c_j cos(j theta)) / (2 h_i^2)
@@ -563,11 +619,12 @@ static int grid_for(long long work, int block, int num_sms)
 // ABI
 
 extern "C" sq_status sq_build_hamiltonian(const sq_grid *grid, const double *d_veff, const sq_atoms *atoms,
-                                          double R_cut, double lambda_min, double lambda_max, void *stream_,
-                                          sq_handle *out)
+                                          double R_cut, int flags, double lambda_min, double lambda_max,
+                                          void *stream_, sq_handle *out)
 {
     g_last_error[0] = 0;
     if (!grid || !d_veff || !atoms || !out) return fail(SQ_ERR_ARG, "null argument");
+    if (flags & ~SQ_GRAD_FD) return fail(SQ_ERR_ARG, "flags %d", flags);
     cudaStream_t stream = (cudaStream_t)stream_;
     for (int a = 0; a < 3; a++)
         if (grid->n[a] < 1 || !(grid->L[a] > 0) || !std::isfinite(grid->L[a]))
@@ -660,10 +717,17 @@ extern "C" sq_status sq_build_hamiltonian(const sq_grid *grid, const double *d_v
             h->natom, d_R, h->L[0], h->L[1], h->L[2], h->n[0], h->n[1], h->n[2], h->sigma, h->rc, h->d_fac64,
             h->fac64_stride, h->fac64_off[0], h->fac64_off[1], h->fac64_off[2]);
         SQ_CUDA(cudaGetLastError());
+        if (flags & SQ_GRAD_FD) {
+            SQ_COUNT(1);
+            k_fd_gradient<<<grid_for(work, 256, h->num_sms), 256, 0, stream>>>(
+                h->natom, h->d_fac64, h->fac64_stride, h->fac64_off[0], h->fac64_off[1], h->fac64_off[2], h->n[0],
+                h->n[1], h->n[2], h->h[0], h->h[1], h->h[2], fd1_coefficients(h->fd_order));
+            SQ_CUDA(cudaGetLastError());
+        }
         SQ_COUNT(1);
         k_support<<<grid_for(3LL * h->natom, 128, h->num_sms), 128, 0, stream>>>(
             h->natom, h->d_fac64, h->fac64_stride, h->fac64_off[0], h->fac64_off[1], h->fac64_off[2], h->n[0],
-            h->n[1], h->n[2], h->d_sup, d_bad + 1);
+            h->n[1], h->n[2], h->d_sup, d_bad + 1, (flags & SQ_GRAD_FD) ? h->p : 0);
         SQ_CUDA(cudaGetLastError());
         const long long work2 = (long long)h->natom * h->fac2_stride;
         SQ_COUNT(2);
@@ -809,6 +873,37 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, long long q0,
     int dev_smem = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
     if constexpr (sizeof(T) == 4) {
+        // FP32 on a cubic 29^3 cube with the 12th-order stencil: the two-CTA cluster kernel, sized by
+        // the largest number of atoms touching one cube
+        if (h->natom > 0 && cluster_supported(h->nc, h->p)) {
+            int *d_cnt = reinterpret_cast<int *>(h->d_small) + 40;   // bytes 160..171 of the small scratch
+            SQ_CUDA(cudaMemsetAsync(d_cnt, 0, 3 * sizeof(int), stream));
+            SQ_COUNT(1);
+            SQ_CUDA(slab_counts(a, d_cnt, h->num_sms, stream));
+            int cnt[2];
+            SQ_CUDA(cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, stream));
+            SQ_CUDA(cudaStreamSynchronize(stream));
+            const int amax = cnt[0] > 0 ? cnt[0] : 1, fmax = cnt[1] > 0 ? cnt[1] : 1;
+            size_t sm = 0;
+            int maxc = 0;
+            if (cluster_prepare(h->nc[0], amax, fmax, &sm, &maxc) == cudaSuccess && sm <= (size_t)dev_smem &&
+                maxc > 0) {
+                long long ncl = maxc;
+                if (ncl > q1 - q0) ncl = q1 - q0;
+                h->kernel_used = 2;
+                SQ_CUDA(cudaEventRecord(h->ev[0], stream));
+                SQ_COUNT(1);
+                SQ_CUDA(launch_cluster(a, amax, fmax, (int)ncl, sm, d_cnt + 2, stream));
+                SQ_CUDA(cudaEventRecord(h->ev[1], stream));
+                dim3 g2(kSumBlocks, K + 1);
+                SQ_COUNT(1);
+                k_msum_partial<T><<<g2, 256, 0, stream>>>(reinterpret_cast<const T *>(h->d_mu), h->N_d, K,
+                                                          h->d_msum_part, q0, q1);
+                SQ_CUDA(cudaGetLastError());
+                return SQ_OK;
+            }
+            cudaGetLastError();   // a configuration the cluster kernel cannot take falls through
+        }
         // FP32 on a cubic 21^3 / 25^3 cube with the 12th-order stencil: the slab kernel, sized by the
         // largest number of atoms touching one cube
         if (h->natom > 0 && slab_supported(h->nc, h->p)) {
@@ -1010,7 +1105,7 @@ static sq_status moments_stage(sq_handle h, int K, int precision, int want_force
         SQ_CUDA(cudaMemcpyAsync(&slab_err, reinterpret_cast<int *>(h->d_small) + 42, sizeof(int),
                                 cudaMemcpyDeviceToHost, stream));
     SQ_CUDA(cudaStreamSynchronize(stream));
-    if (slab_err) return fail(SQ_ERR_UNSUPPORTED, "a column exceeded the slab kernel's atom capacity (%d)", slab_err);
+    if (slab_err) return fail(SQ_ERR_UNSUPPORTED, "a column exceeded the FP32 kernel's atom capacity (%d)", slab_err);
     if (bad) return fail(SQ_ERR_NOT_FINITE, "moment sums are not finite");
     SQ_CUDA(cudaEventElapsedTime(&h->t_rec, h->ev[0], h->ev[1]));
     SQ_CUDA(cudaEventElapsedTime(&h->t_msum, h->ev[1], h->ev[2]));
@@ -1304,6 +1399,7 @@ extern "C" const char *sq_kernel_name(sq_handle h)
 {
     if (!h || !h->have_density) return "";
     if (h->kernel_used == 1) return h->nc[0] == 21 ? "slab_kernel<21,6>" : "slab_kernel<25,6>";
+    if (h->kernel_used == 2) return "cluster_kernel<29,6>";
     return h->precision == SQ_FP64 ? "recursion_kernel<double>" : "recursion_kernel<float>";
 }
 
@@ -1494,6 +1590,8 @@ struct sq_batch_s {
     int slab_ready = 0, ngeneric = 0;
     std::vector<int> slab_amax, slab_fmax;
     std::vector<size_t> slab_smem;
+    std::vector<int> slab_kind;               // 1: slab kernel (21^3, 25^3), 2: cluster kernel (29^3)
+    std::vector<int> slab_ncl;                // clusters of a cluster launch
 };
 
 extern "C" void sq_batch_destroy(sq_batch b)
@@ -1679,8 +1777,12 @@ static sq_status batch_enqueue(sq_batch b, const RecursionArgs<T> *host_args, do
             int *d_err = reinterpret_cast<int *>(h->d_small) + 42;
             SQ_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), stream));
             SQ_COUNT(1);
-            SQ_CUDA(launch_slab(host_args[i], b->slab_amax[i], b->slab_fmax[i], (int)std::min<long long>(h->num_sms, h->N_d),
-                                b->slab_smem[i], d_err, stream));
+            if (b->slab_kind[i] == 2)
+                SQ_CUDA(launch_cluster(host_args[i], b->slab_amax[i], b->slab_fmax[i],
+                                       (int)std::min<long long>(b->slab_ncl[i], h->N_d), b->slab_smem[i], d_err, stream));
+            else
+                SQ_CUDA(launch_slab(host_args[i], b->slab_amax[i], b->slab_fmax[i],
+                                    (int)std::min<long long>(h->num_sms, h->N_d), b->slab_smem[i], d_err, stream));
         }
     }
     // per-cell moment sums, Fermi level (fixed number of bisection launches), weights and density
@@ -1728,12 +1830,15 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
         b->slab_amax.assign(nc, 0);
         b->slab_fmax.assign(nc, 0);
         b->slab_smem.assign(nc, 0);
+        b->slab_kind.assign(nc, 0);
+        b->slab_ncl.assign(nc, 0);
         if constexpr (sizeof(T) == 4) {
             int dev_smem = 0;
             cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->cells[0]->dev);
             for (int i = 0; i < nc; i++) {
                 sq_handle h = b->cells[i];
-                if (h->natom == 0 || !slab_supported(h->nc, h->p)) continue;
+                const bool cl = cluster_supported(h->nc, h->p);
+                if (h->natom == 0 || !(cl || slab_supported(h->nc, h->p))) continue;
                 int *d_cnt = reinterpret_cast<int *>(h->d_small) + 40;
                 SQ_CUDA(cudaMemsetAsync(d_cnt, 0, 3 * sizeof(int), b->cap_stream));
                 SQ_COUNT(1);
@@ -1742,11 +1847,23 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
                 SQ_CUDA(cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, b->cap_stream));
                 SQ_CUDA(cudaStreamSynchronize(b->cap_stream));
                 const int amax = cnt[0] > 0 ? cnt[0] : 1, fmax = cnt[1] > 0 ? cnt[1] : 1;
-                const size_t sm = slab_smem_bytes(h->nc[0], amax, fmax);
-                if (sm > (size_t)dev_smem) continue;
+                size_t sm = 0;
+                int maxc = 0;
+                if (cl) {
+                    if (cluster_prepare(h->nc[0], amax, fmax, &sm, &maxc) != cudaSuccess || maxc < 1 ||
+                        sm > (size_t)dev_smem) {
+                        cudaGetLastError();
+                        continue;
+                    }
+                } else {
+                    sm = slab_smem_bytes(h->nc[0], amax, fmax);
+                    if (sm > (size_t)dev_smem) continue;
+                }
                 b->slab_amax[i] = amax;
                 b->slab_fmax[i] = fmax;
                 b->slab_smem[i] = sm;
+                b->slab_kind[i] = cl ? 2 : 1;
+                b->slab_ncl[i] = maxc;
             }
         }
         b->ngeneric = 0;
@@ -1829,7 +1946,7 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
         SQ_CUDA(cudaMemcpy(&bad, h->d_small, sizeof(int), cudaMemcpyDeviceToHost));
         SQ_CUDA(cudaMemcpy(&fin, st, sizeof(fin), cudaMemcpyDeviceToHost));
         if (bad) return fail(SQ_ERR_NOT_FINITE, "cell %d: moment sums are not finite", i);
-        h->kernel_used = b->slab_amax[i] > 0 ? 1 : 0;
+        h->kernel_used = b->slab_amax[i] > 0 ? b->slab_kind[i] : 0;
         if (h->kernel_used) {
             int slab_err = 0;
             SQ_CUDA(cudaMemcpy(&slab_err, reinterpret_cast<int *>(h->d_small) + 42, sizeof(int), cudaMemcpyDeviceToHost));

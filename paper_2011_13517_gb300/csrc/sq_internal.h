@@ -118,4 +118,12 @@ cudaError_t launch_slab_adjoint(const RecursionArgs<float> &args, int amax, int 
                                 long long scratch_stride, cudaStream_t stream);
 long long slab_vector_floats(int nc);
 
+// FP32 cluster kernel (cubic 29^3 cubes, 12th-order FD): a cluster of two CTAs per column, each
+// holding half of the cube's y-slabs.  Uses the slab kernel's capacity pre-pass (slab_counts).
+// cluster_prepare gives the shared memory per CTA and how many clusters fit on the GPU at once.
+bool cluster_supported(const int nc[3], int fd_half);
+cudaError_t cluster_prepare(int nc, int amax, int fmax, size_t *smem, int *max_clusters);
+cudaError_t launch_cluster(const RecursionArgs<float> &args, int amax, int fmax, int nclusters, size_t smem,
+                           int *err, cudaStream_t stream);
+
 }  // namespace sq

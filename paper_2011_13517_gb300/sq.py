@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libsq.so")
 SQ_FP64 = 0
 SQ_FP32 = 1
 SQ_WANT_FORCE = 1
+SQ_GRAD_ANALYTIC = 0
+SQ_GRAD_FD = 1
 
 STATUS = {0: "SQ_OK", 1: "SQ_ERR_ARG", 2: "SQ_ERR_CUBE_EXCEEDS_BOX", 3: "SQ_ERR_NO_BRACKET",
           4: "SQ_ERR_NOT_FINITE", 5: "SQ_ERR_CUDA", 6: "SQ_ERR_TIMEOUT", 7: "SQ_ERR_OOM",
@@ -60,7 +62,7 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
         L.sq_build_hamiltonian.argtypes = [ctypes.POINTER(sq_grid), vp, ctypes.POINTER(sq_atoms), ctypes.c_double,
-                                           ctypes.c_double, ctypes.c_double, vp, ctypes.POINTER(vp)]
+                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, vp, ctypes.POINTER(vp)]
         L.sq_density.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                  vp, dp, vp]
         d = ctypes.c_double
@@ -146,9 +148,10 @@ class Handle:
 
 
 def sq_build_hamiltonian(n, L, fd_order, d_veff, R, lmax, sigma, rc, energy, R_cut,
-                         lambda_min=math.nan, lambda_max=math.nan, stream=None) -> Handle:
+                         lambda_min=math.nan, lambda_max=math.nan, stream=None, flags=SQ_GRAD_ANALYTIC) -> Handle:
     """sq_build_hamiltonian: grid (n, L, fd_order), device V_eff [N_d] float64, atoms R [natom, 3]
-    with projector parameters, truncation half-width R_cut, optional spectral bounds."""
+    with projector parameters, truncation half-width R_cut, optional spectral bounds, and the
+    projector gradient of the force (flags: SQ_GRAD_ANALYTIC or SQ_GRAD_FD)."""
     g = sq_grid()
     for a in range(3):
         g.n[a] = int(n[a])
@@ -166,7 +169,8 @@ def sq_build_hamiltonian(n, L, fd_order, d_veff, R, lmax, sigma, rc, energy, R_c
     N_d = int(g.n[0]) * int(g.n[1]) * int(g.n[2])
     out = ctypes.c_void_p()
     _check(lib().sq_build_hamiltonian(ctypes.byref(g), _dev_ptr(d_veff, numel=N_d), ctypes.byref(at), float(R_cut),
-                                      float(lambda_min), float(lambda_max), _stream(stream), ctypes.byref(out)))
+                                      int(flags), float(lambda_min), float(lambda_max), _stream(stream),
+                                      ctypes.byref(out)))
     return Handle(out.value, N_d=N_d, natom=at.natom, nproj=1 if int(lmax) == 0 else 4)
 
 
@@ -368,17 +372,18 @@ def sq_copy_moments(h: Handle, N_d, stream=None):
 # ---------------------------------------------------------------------------------------------
 # convenience for a generated cell (marshalling only)
 
-def build_for_cell(cell, bounds=None, stream=None, d_veff=None):
+def build_for_cell(cell, bounds=None, stream=None, d_veff=None, flags=SQ_GRAD_ANALYTIC):
     if d_veff is None:
         d_veff = torch.from_numpy(np.ascontiguousarray(cell.veff.reshape(-1))).to("cuda")
     lo, hi = (math.nan, math.nan) if bounds is None else bounds
     return sq_build_hamiltonian(cell.n, cell.box, cell.fd_order, d_veff, cell.R, cell.lmax, cell.proj_sigma,
-                                cell.proj_rc, cell.proj_energy, cell.R_cut, lo, hi, stream=stream)
+                                cell.proj_rc, cell.proj_energy, cell.R_cut, lo, hi, stream=stream, flags=flags)
 
 
-def solve_cell(cell, precision=SQ_FP64, force=True, bounds=None, K=None, kT=None, N_e=None, stream=None):
+def solve_cell(cell, precision=SQ_FP64, force=True, bounds=None, K=None, kT=None, N_e=None, stream=None,
+               grad=SQ_GRAD_ANALYTIC):
     """Build + density (+ energy, force) for one cell; returns numpy results."""
-    h = build_for_cell(cell, bounds=bounds, stream=stream)
+    h = build_for_cell(cell, bounds=bounds, stream=stream, flags=grad)
     try:
         rho = torch.empty(cell.N_d, dtype=torch.float64, device="cuda")
         lam_f = sq_density(h, cell.K if K is None else K, cell.kT if kT is None else kT,

@@ -2,6 +2,7 @@
 
 Calls only oracle/ (and the seeded input generator).  Usage:
     python tests/golden/make_golden.py vacancy [--threads N]
+    python tests/golden/make_golden.py batch_23          # cell 23 of the 32-cell batch workload
 The vacancy cell (118,944 grid points, K = 60, 25^3 cubes) takes about an hour of 8-core CPU time.
 """
 import argparse
@@ -23,12 +24,15 @@ WORKLOADS = {"tiny": cells.tiny_cell, "vacancy": cells.vacancy_cell, "precision"
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("workload", choices=sorted(WORKLOADS))
+    ap.add_argument("workload", help="tiny, vacancy, precision or batch_<i> (cell i of cells.batch_cells(32))")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--refresh-digest", action="store_true",
                     help="only recompute the input digest field of an existing file")
     args = ap.parse_args()
-    cell = WORKLOADS[args.workload]()
+    if args.workload.startswith("batch_"):
+        cell = cells.batch_cells(32)[int(args.workload.split("_")[1])]
+    else:
+        cell = WORKLOADS[args.workload]()
     if args.refresh_digest:
         path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{cell.name}.json")
         data = json.load(open(path))

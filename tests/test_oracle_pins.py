@@ -364,3 +364,84 @@ def test_hcp_symmetry_of_truncated_density():
     }
     for name, t in tests.items():
         assert np.max(np.abs(t - rho)) < 1e-12 * scale, name
+
+
+# --- the finite-difference gradient of the nonlocal force (Sec. 3 "Atomic forces") --------------
+
+@pytest.mark.parametrize("order,expected", [
+    (2, [0.0, 1.0 / 2.0]),
+    (4, [0.0, 2.0 / 3.0, -1.0 / 12.0]),
+    (6, [0.0, 3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0]),
+    (8, [0.0, 4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0]),
+])
+def test_fd1_coeffs_textbook(order, expected):
+    np.testing.assert_allclose(oracle.fd1_coeffs(order), expected, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8, 10, 12])
+def test_fd1_coeffs_exact_on_polynomials(order):
+    """sum_j a_j (j^s - (-j)^s) is the exact first derivative of x^s at 0 (1 for s = 1, else 0) for
+    every s <= order."""
+    a = oracle.fd1_coeffs(order)
+    p = order // 2
+    for s in range(order + 1):
+        val = sum(a[j] * (float(j) ** s - float(-j) ** s) for j in range(1, p + 1))
+        exact = 1.0 if s == 1 else 0.0
+        assert abs(val - exact) < 1e-9 * max(1.0, p ** s), (s, val)
+
+
+def _periodic_fd_gradient(f3, h, a):
+    """D_h f on the full periodic grid, f3 indexed [z][y][x]: plain np.roll differences per axis."""
+    out = []
+    for d, ax in ((0, 2), (1, 1), (2, 0)):
+        g = np.zeros_like(f3)
+        for j in range(1, len(a)):
+            g += a[j] * (np.roll(f3, -j, axis=ax) - np.roll(f3, j, axis=ax))
+        out.append(g / h[d])
+    return out
+
+
+def test_fd_gradient_force_moments_match_dense_cube_eigendecomposition():
+    """The oracle's force moments with the FD gradient (separable D_h tables) against an independent
+    route: D_h chi by 3D np.roll differences of the dense projectors, and T_k(Hhat_q) e_q from the
+    eigendecomposition of each dense cube operator; A_k = sum_q chi(x_q) (D_h chi)_{C_q}^T v_k^q."""
+    c = pin_cell(lmax=1, m=2, K=6)
+    lo, hi = oracle.spectral_bounds(c)
+    omega, tau = oracle.scale_shift(lo, hi)
+    _, A = oracle.moments(c, omega, tau, K=c.K, force=True, grad_fd=True)
+    chi = oracle.projectors(c)
+    a = oracle.fd1_coeffs(c.fd_order)
+    H = dense.hamiltonian(c, chi)
+    shape = (int(c.n[2]), int(c.n[1]), int(c.n[0]))
+    Dchi = np.zeros((c.natom, chi.shape[1], 3, c.N_d))
+    for J in range(c.natom):
+        for lm in range(chi.shape[1]):
+            for d, g in enumerate(_periodic_fd_gradient(chi[J, lm].reshape(shape), c.h, a)):
+                Dchi[J, lm, d] = g.reshape(-1)
+    ref = np.zeros_like(A)
+    for q in range(c.N_d):
+        gidx = oracle.cube_indices(c, q)
+        Hq = (H[np.ix_(gidx, gidx)] - omega * np.eye(gidx.size)) / tau
+        lam, U = np.linalg.eigh(Hq)
+        lam = np.clip(lam, -1.0, 1.0)
+        centre = int(np.flatnonzero(gidx == q)[0])
+        for k in range(c.K + 1):
+            vk = U @ (np.cos(k * np.arccos(lam)) * U[centre])
+            ref[k] += np.einsum("jl,jldx,x->jld", chi[:, :, q], Dchi[:, :, :, gidx], vk)
+    np.testing.assert_allclose(A, ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+
+
+def test_fd_gradient_force_approaches_analytic_as_h_shrinks():
+    """D_h chi -> grad chi at order n_o in h: the FD-gradient force approaches the analytic-gradient
+    force of the same truncated SQ as the grid is refined (h = 0.9, 0.7, 0.55 bohr, 6th order)."""
+    diffs = []
+    for h in (0.9, 0.7, 0.55):
+        c = cells.make_cell("gfd", (1, 1, 1), h, 6, 1, 0.0, 8, 0.01, seed=3)
+        c.R_cut = float(2 * np.mean(c.h))
+        assert np.all(c.m == 2)
+        lo, hi = oracle.spectral_bounds(c)
+        fa = oracle.sq_solve(c, force=True, bounds=(lo, hi))["force"]
+        ff = oracle.sq_solve(c, force=True, bounds=(lo, hi), grad_fd=True)["force"]
+        diffs.append(float(np.max(np.abs(ff - fa))) / float(np.max(np.abs(fa))))
+    assert diffs[0] > 2.0 * diffs[1] > 4.0 * diffs[2], diffs
+    assert diffs[2] < 1e-2, diffs
