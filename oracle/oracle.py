@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY.  This package is the independent reference the CUDA li
 against; only tests/, the package smoke check and bench.py's CPU-baseline leg may import it.  It
 shares no code with the CUDA path: the per-column recursion is plain C (sq_oracle.c, OpenMP over
 grid points); the steps after it (moment sums, Chebyshev coefficients, Fermi level, density,
-energy, force) are plain numpy below, each written from the paper's definition.
+energy, force) are plain numpy below, each written from the paper's definition.  The Gauss
+(Lanczos) quadrature path for rho, U and S (lanczos, gauss_rule, gauss_fermi_level, gauss_solve) is
+the paper's own density method; its Jacobi eigendecomposition uses scipy's tridiagonal eigensolver.
 
 Paper: Ghosh & Bhattacharya, arXiv 2011.13517.  Sections cited below:
   Sec. 2.1  density-operator KS-DFT, Fermi-Dirac fixed point (Eq. FixedPoint), free energy,
@@ -73,6 +75,8 @@ def lib():
         _lib.sq_oracle_moments.argtypes = [ctypes.POINTER(_Problem), ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int, ctypes.c_long, lp, dp, dp, ctypes.c_int]
         _lib.sq_oracle_max_threads.restype = ctypes.c_int
+        _lib.sq_oracle_lanczos.argtypes = [ctypes.POINTER(_Problem), ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_long, lp, dp, dp, ctypes.c_int]
         _lib.sq_oracle_tangent.argtypes = [ctypes.POINTER(_Problem), ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                            dp, ctypes.c_long, lp, dp, ctypes.c_int]
     return _lib
@@ -441,3 +445,92 @@ def sq_tangent(cell, dV, bounds=None, K=None):
     drho = 2.0 * (dmu @ r["c"] + dlam * (r["mu"] @ cp)) / r["dV"]
     dU = 2.0 * (float(np.dot(r["d"], dM)) + dlam * float(np.dot(dp, r["Msum"])))
     return drho, dU, dlam, r
+
+
+# --------------------------------------------------------------------------------------------
+# Gauss (Lanczos) spectral quadrature for rho, U and S (Sec. 2.2 "Spectral Gauss quadrature",
+# Eq. Lanczos; Sec. 3 Eq. Ne and "Spectral weights, nodes and electronic fields")
+
+def lanczos(cell, omega, tau, K=None, cols=None, nthreads=0, full=False, m=None):
+    """Lanczos coefficients (a [ncols, K], b [ncols, K]) of the scaled truncated operator of each
+    column, started from e_q (Eq. Lanczos): a_{k+1} = (Hhat v_k, v_k), b_{k+1} = ||(Hhat - a_{k+1}) v_k
+    - b_k v_{k-1}||.  Zeros after an exact breakdown (b = 0)."""
+    K = cell.K if K is None else K
+    cols = np.arange(cell.N_d, dtype=np.int64) if cols is None else np.ascontiguousarray(cols, dtype=np.int64)
+    prob = Problem(cell, full=full, m=m)
+    a = np.zeros((cols.size, K))
+    b = np.zeros((cols.size, K))
+    rc = lib().sq_oracle_lanczos(ctypes.byref(prob.st), float(omega), float(tau), int(K), int(cols.size), _lp(cols),
+                                 _dp(a), _dp(b), int(nthreads))
+    if rc:
+        raise RuntimeError(f"sq_oracle_lanczos failed ({rc})")
+    return a, b
+
+
+def gauss_rule(a, b, omega, tau):
+    """Spectral nodes and weights of each column from its Jacobi matrix J_K = tridiag(b; a; b): the
+    nodes are the eigenvalues, the weights the squared first components of the normalised
+    eigenvectors (Sec. 2.2; the printed sentence swaps the two symbols).  Nodes are returned in the
+    unscaled energy, lambda = tau lambda_hat + omega.  A column whose b_k vanishes (exhausted Krylov
+    space) uses the leading k x k block; its other nodes get weight 0.
+    Returns (nodes [ncols, K], weights [ncols, K])."""
+    from scipy.linalg import eigh_tridiagonal
+    ncols, K = a.shape
+    nodes = np.zeros((ncols, K))
+    weights = np.zeros((ncols, K))
+    for i in range(ncols):
+        n = K
+        for k in range(K - 1):
+            if b[i, k] == 0.0:
+                n = k + 1
+                break
+        lam, vec = eigh_tridiagonal(a[i, :n], b[i, :n - 1])
+        nodes[i, :n] = tau * lam + omega
+        nodes[i, n:] = omega
+        weights[i, :n] = vec[0, :] ** 2
+    return nodes, weights
+
+
+def gauss_electron_count(lam_f, nodes, weights, kT):
+    """N(lambda_f) = 2 sum_q sum_k w_k^q g(lambda_k^q, lambda_f) (Eq. Ne)."""
+    return 2.0 * float(np.sum(weights * fermi(nodes, lam_f, kT)))
+
+
+def gauss_fermi_level(nodes, weights, kT, N_e, lmin, lmax):
+    """Root of N(lambda_f) = N_e by bisection on [lmin, lmax] (the paper uses Brent's method; the
+    same deterministic rule as the Chebyshev path: mid = lo + (hi - lo)/2, lo = mid if N(mid) < N_e
+    else hi = mid, until the midpoint no longer separates the bracket, at most 200 steps)."""
+    lo, hi = lmin, lmax
+    if gauss_electron_count(lo, nodes, weights, kT) > N_e or gauss_electron_count(hi, nodes, weights, kT) < N_e:
+        raise ValueError("electron count not bracketed")
+    x = lo + 0.5 * (hi - lo)
+    for _ in range(200):
+        if gauss_electron_count(x, nodes, weights, kT) < N_e:
+            lo = x
+        else:
+            hi = x
+        x = lo + 0.5 * (hi - lo)
+        if x <= lo or x >= hi:
+            break
+    return x
+
+
+def gauss_solve(cell, bounds=None, nthreads=0, full=False, K=None):
+    """Gauss (Lanczos) SQ for one cell: spectral nodes and weights at every grid point, the Fermi
+    level (Eq. Ne), and rho^q = 2 sum_k w_k g(lambda_k) (Eq. rhoq, electrons per point; rho = rho^q/dV
+    per bohr^3), U = sum_q u^q with u^q = 2 sum_k w_k lambda_k g(lambda_k) (Eq. uq; the printed
+    approximation drops the integral's factor 2), S = sum_q s^q with s^q = -2 sum_k w_k s(lambda_k)
+    (Eq. sq, units of k_B), F = U - kT S."""
+    K = cell.K if K is None else K
+    lmin, lmax = spectral_bounds(cell) if bounds is None else bounds
+    omega, tau = scale_shift(lmin, lmax)
+    dV = float(np.prod(cell.box / cell.n))
+    a, b = lanczos(cell, omega, tau, K=K, nthreads=nthreads, full=full)
+    nodes, weights = gauss_rule(a, b, omega, tau)
+    lam_f = gauss_fermi_level(nodes, weights, cell.kT, cell.N_e, lmin, lmax)
+    g = fermi(nodes, lam_f, cell.kT)
+    rho_q = 2.0 * np.sum(weights * g, axis=1)
+    U = 2.0 * float(np.sum(weights * nodes * g))
+    S = -2.0 * float(np.sum(weights * entropy_density(nodes, lam_f, cell.kT)))
+    return dict(lmin=lmin, lmax=lmax, omega=omega, tau=tau, K=K, a=a, b=b, nodes=nodes, weights=weights,
+                lam_f=lam_f, rho=rho_q / dV, U=U, S=S, F=U - cell.kT * S, dV=dV)

@@ -18,7 +18,9 @@
  *  - the Chebyshev three-term recursion v_0 = e_q, v_1 = Hhat v_0, v_{k+1} = 2 Hhat v_k - v_{k-1}
  *    (Eq. Chebyshev, Sec. 2.2), its moments mu_k^q = v_k(q);
  *  - the nonlocal-force moments A_k^{J,lm,d} = sum_q chi_Jlm(x_q) sum_x d_d chi_Jlm(x) v_k^q(x)
- *    (Eq. NLforceSQ and the discrete nonlocal force of Sec. 3 "Atomic forces").
+ *    (Eq. NLforceSQ and the discrete nonlocal force of Sec. 3 "Atomic forces");
+ *  - the Lanczos coefficients a_k, b_k of the same truncated operator started from e_q (Eq. Lanczos,
+ *    Sec. 2.2), whose Jacobi matrices give the Gauss quadrature nodes and weights (oracle.py).
  *
  * Readings where the paper is silent or ambiguous:
  *  - the recursion starts from the Euclidean unit vector e_q, so mu_0 = 1;
@@ -658,6 +660,93 @@ int sq_oracle_tangent(const sq_oracle_problem *P, double omega, double tau, int 
             }
         }
         free(v0); free(v1); free(d0); free(d1); free(t1); free(t2); free(dloc);
+    }
+    ctx_free(&C);
+    return err ? -4 : 0;
+}
+
+/*
+ * Lanczos iteration of Sec. 2.2 (Eq. Lanczos) on the truncated scaled operator Hhat_q of each given
+ * column, started from the unit vector at the column's own point (eta_q = e_q):
+ *     v_{-1} = 0, v_0 = e_q, b_0 v_{-1} = 0,
+ *     a_{k+1} = (Hhat v_k, v_k),
+ *     b_{k+1} v_{k+1} = (Hhat - a_{k+1}) v_k - b_k v_{k-1},   b_{k+1} = || that vector ||,
+ * for k = 0 .. K-1, without reorthogonalisation (the paper states none).  The Jacobi matrix of the
+ * column is tridiag(b_1..b_{K-1}; a_1..a_K; b_1..b_{K-1}); the Gauss nodes and weights follow from
+ * its eigendecomposition (oracle.py).  When b_{k+1} = 0 the Krylov space is exhausted: the remaining
+ * a and b are written as 0 and the caller truncates the Jacobi matrix there.
+ *   a, b   [ncols][K]: a_1..a_K and b_1..b_K of the scaled operator (Hhat = (H - omega)/tau)
+ */
+int sq_oracle_lanczos(const sq_oracle_problem *P, double omega, double tau, int K, long ncols, const long *cols,
+                      double *a, double *b, int nthreads)
+{
+    oracle_ctx C;
+    int rc = ctx_init(&C, P);
+    if (rc) return rc;
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel
+    {
+        double *vm = (double *)malloc(sizeof(double) * C.nc3), *v = (double *)malloc(sizeof(double) * C.nc3);
+        double *w = (double *)malloc(sizeof(double) * C.nc3);
+        if (!vm || !v || !w) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (long ic = 0; ic < ncols; ic++) {
+                long q = cols[ic];
+                int q3[3];
+                unravel(P, q, q3);
+                column_atoms ca;
+                if (column_atoms_build(&C, q3, &ca)) {
+#pragma omp atomic write
+                    err = 1;
+                    continue;
+                }
+                double *ak = a + ic * K, *bk = b + ic * K;
+                memset(vm, 0, sizeof(double) * C.nc3);
+                memset(v, 0, sizeof(double) * C.nc3);
+                v[centre_local(&C)] = 1.0;
+                double bprev = 0.0;
+                int done = 0;
+                for (int k = 0; k < K; k++) {
+                    if (done) {
+                        ak[k] = 0.0;
+                        bk[k] = 0.0;
+                        continue;
+                    }
+                    apply_hhat(&C, q3, &ca, omega, tau, v, w);
+                    double alpha = 0.0;
+                    for (long i = 0; i < C.nc3; i++) alpha += w[i] * v[i];
+                    double nrm = 0.0;
+                    for (long i = 0; i < C.nc3; i++) {
+                        w[i] = w[i] - alpha * v[i] - bprev * vm[i];
+                        nrm += w[i] * w[i];
+                    }
+                    double beta = sqrt(nrm);
+                    ak[k] = alpha;
+                    bk[k] = beta;
+                    if (beta == 0.0) {
+                        done = 1;
+                        continue;
+                    }
+                    for (long i = 0; i < C.nc3; i++) {
+                        vm[i] = v[i];
+                        v[i] = w[i] / beta;
+                    }
+                    bprev = beta;
+                }
+                column_atoms_free(&ca);
+            }
+        }
+        free(vm);
+        free(v);
+        free(w);
     }
     ctx_free(&C);
     return err ? -4 : 0;

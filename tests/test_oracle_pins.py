@@ -445,3 +445,83 @@ def test_fd_gradient_force_approaches_analytic_as_h_shrinks():
         diffs.append(float(np.max(np.abs(ff - fa))) / float(np.max(np.abs(fa))))
     assert diffs[0] > 2.0 * diffs[1] > 4.0 * diffs[2], diffs
     assert diffs[2] < 1e-2, diffs
+
+
+# --- Gauss (Lanczos) spectral quadrature (Sec. 2.2 "Spectral Gauss quadrature", Eq. Lanczos) -------
+
+def _dense_cube(c, q, omega, tau):
+    H = dense.hamiltonian(c, oracle.projectors(c) if c.natom else None)
+    gidx = oracle.cube_indices(c, q)
+    Hq = (H[np.ix_(gidx, gidx)] - omega * np.eye(gidx.size)) / tau
+    lam, U = np.linalg.eigh(Hq)
+    centre = int(np.flatnonzero(gidx == q)[0])
+    return lam, U[centre] ** 2
+
+
+def test_gauss_rule_integrates_polynomials_exactly():
+    """A K-node Gauss rule of the spectral measure of e_q is exact for polynomials of degree 2K-1:
+    sum_k w_k lam_k^j = (Hhat_q^j)_qq for j <= 2K - 1, with the right side from the eigendecomposition
+    of the dense cube operator.  The weights sum to 1 (||e_q|| = 1)."""
+    c = pin_cell(lmax=1, m=2, K=7)
+    lo, hi = oracle.spectral_bounds(c)
+    omega, tau = oracle.scale_shift(lo, hi)
+    cols = np.array([0, 17, 400, c.N_d - 1])
+    a, b = oracle.lanczos(c, omega, tau, K=c.K, cols=cols)
+    nodes, w = oracle.gauss_rule(a, b, 0.0, 1.0)          # scaled nodes
+    for i, q in enumerate(cols):
+        lam, wq = _dense_cube(c, q, omega, tau)
+        assert abs(w[i].sum() - 1.0) < 1e-13
+        for j in range(2 * c.K):
+            exact = float(np.dot(wq, lam ** j))
+            assert abs(float(np.dot(w[i], nodes[i] ** j)) - exact) < 1e-12, (q, j)
+    # and not beyond: degree 2K differs
+    lam, wq = _dense_cube(c, cols[0], omega, tau)
+    assert abs(float(np.dot(w[0], nodes[0] ** (2 * c.K))) - float(np.dot(wq, lam ** (2 * c.K)))) > 1e-12
+
+
+def test_gauss_rule_with_the_whole_krylov_space_is_exact():
+    """With K equal to the cube's dimension (m = 1: 27 points) the Krylov space of e_q is the whole
+    cube, so the Gauss rule reproduces the spectral measure itself: rho^q = 2 g(H_q)_qq for any
+    Fermi level, from the dense cube eigendecomposition."""
+    c = pin_cell(lmax=1, m=1, K=27)
+    lo, hi = oracle.spectral_bounds(c)
+    omega, tau = oracle.scale_shift(lo, hi)
+    cols = np.array([5, 300, 777])
+    a, b = oracle.lanczos(c, omega, tau, K=c.K, cols=cols)
+    nodes, w = oracle.gauss_rule(a, b, omega, tau)
+    for lam_f in (-0.3, 0.2, 0.9):
+        for i, q in enumerate(cols):
+            lam, wq = _dense_cube(c, q, omega, tau)
+            exact = 2.0 * float(np.dot(wq, oracle.fermi(tau * lam + omega, lam_f, c.kT)))
+            got = 2.0 * float(np.dot(w[i], oracle.fermi(nodes[i], lam_f, c.kT)))
+            assert abs(got - exact) < 1e-10, (q, lam_f, got, exact)
+
+
+def test_gauss_sum_rule_and_entropy_sign():
+    c = cells.tiny_cell()
+    r = oracle.gauss_solve(c)
+    assert abs(r["rho"].sum() * r["dV"] - c.N_e) < 1e-11 * c.N_e
+    assert r["S"] >= 0.0
+    np.testing.assert_allclose(r["weights"].sum(axis=1), 1.0, rtol=0, atol=1e-12)
+
+
+@pytest.mark.slow
+def test_untruncated_gauss_converges_faster_than_chebyshev():
+    """No truncation (the cube is the whole box): Gauss quadrature converges to the exact dense
+    finite-temperature density as K grows, and at the same K it is more accurate than the
+    Clenshaw-Curtis (Chebyshev) expansion (the paper's observation in Sec. 4, Table 1)."""
+    c = pin_cell(lmax=0, kT=0.1)
+    ref = dense.solve(c, force=False)
+    lo, hi = oracle.spectral_bounds(c)
+    eg, ec = [], []
+    for K in (10, 20, 40):
+        g = oracle.gauss_solve(c, bounds=(lo, hi), full=True, K=K)
+        ch = oracle.sq_solve(c, force=False, bounds=(lo, hi), full=True, K=K)
+        eg.append(float(np.max(np.abs(g["rho"] - ref["rho"]))))
+        ec.append(float(np.max(np.abs(ch["rho"] - ref["rho"]))))
+    assert eg[0] > eg[1] > eg[2] and eg[2] < 1e-6 * np.max(ref["rho"]), eg
+    assert all(x < y for x, y in zip(eg, ec)), (eg, ec)
+    g20 = oracle.gauss_solve(c, bounds=(lo, hi), full=True, K=20)
+    g40 = oracle.gauss_solve(c, bounds=(lo, hi), full=True, K=40)
+    assert abs(g40["U"] - ref["U"]) < abs(g20["U"] - ref["U"]) and abs(g40["U"] - ref["U"]) < 1e-5
+    assert abs(g40["lam_f"] - ref["lam_f"]) < 1e-6
