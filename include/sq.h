@@ -51,8 +51,15 @@ typedef enum {
  * Moment sums, Chebyshev weights, the Fermi solve, rho, U, S and forces are always FP64. */
 enum { SQ_FP64 = 0, SQ_FP32 = 1 };
 
-/* flags of sq_density */
-enum { SQ_WANT_FORCE = 1 };
+/* flags of sq_density.
+ * SQ_WANT_FORCE: also accumulate the force moments (Chebyshev path only).
+ * SQ_GAUSS: Gauss quadrature (the paper's LSSGQ, Sec. 2.2 "Spectral Gauss quadrature") instead of the
+ *   Chebyshev expansion for rho, U and S: per grid point K Lanczos steps (Eq. Lanczos) on the
+ *   truncated operator from e_q, the Jacobi matrix's eigenvalues as nodes and squared first
+ *   eigenvector components as weights, the Fermi level over all nodes (Eq. Ne), and rho^q, u^q, s^q
+ *   (Eqs. rhoq, uq, sq).  K <= 256; not combinable with SQ_WANT_FORCE (the paper takes the force
+ *   from the Clenshaw-Curtis path); sq_energy then reports the Gauss U and S. */
+enum { SQ_WANT_FORCE = 1, SQ_GAUSS = 2 };
 
 /* flags of sq_build_hamiltonian: the gradient of the projectors in the nonlocal force.
  * SQ_GRAD_ANALYTIC: the analytic gradient of chi.
@@ -172,6 +179,22 @@ sq_status sq_fermi_weights(double lambda_f, int K, double omega, double tau, dou
                            double *e);
 
 /*
+ * sq_gauss_rule -- the Gauss rule of one grid point from its Lanczos coefficients (Sec. 2.2; host,
+ * FP64, pure): the nodes are the eigenvalues of the Jacobi matrix tridiag(b_1..b_{K-1}; a_1..a_K;
+ * b_1..b_{K-1}) mapped back to energies (lambda = tau lambda_hat + omega when a, b are those of the
+ * scaled operator (H - omega)/tau; pass omega = 0, tau = 1 for unscaled coefficients), the weights
+ * the squared first components of its normalised eigenvectors.  The matrix is cut at the first
+ * b_k = 0 (k < K); the nodes past the cut get weight 0.  The same routine runs per column on the GPU
+ * under SQ_GAUSS.
+ *   a, b        host [K] coefficients a_1..a_K, b_1..b_K (b_K unused)
+ *   nodes, weights  host [K] outputs
+ * Errors: SQ_ERR_ARG (K outside 1..256, bad scale), SQ_ERR_NOT_FINITE (non-finite input, or the
+ * eigensolve did not converge).
+ */
+sq_status sq_gauss_rule(const double *a, const double *b, int K, double omega, double tau, double *nodes,
+                        double *weights);
+
+/*
  * sq_fermi_resolve -- re-solve the electron-count equation (Eq. Ne) for a new kT / N_e from the
  * moment sums stored by the last whole-grid sq_density, on the device, and refresh the stored weights;
  * d_rho (may be NULL) receives the matching density.  Same bisection rule as sq_density.
@@ -209,6 +232,18 @@ sq_status sq_fermi_resolve(sq_handle h, double kT, double N_e, double *d_rho, do
  */
 sq_status sq_moments_range(sq_handle h, int K, int precision, int flags, long long q_begin, long long q_end,
                            double *msum, double *A, void *stream);
+
+/*
+ * sq_moments_cols -- the recursion (Eq. Chebyshev) for a list of columns: the moments mu_k^q of the
+ * grid points d_cols[0..ncols), written compactly to d_mu_out [K+1][ncols] (recursion precision, 8 or
+ * 4 bytes per value, caller-owned device buffer).  For callers that need a few columns, e.g. the
+ * columns whose cubes contain one grid point (those are the only ones a change of V_eff there can
+ * move).  Runs the generic column kernel; no sums, no Fermi level; leaves the handle without a
+ * density.  Indices must be distinct and in [0, N_d) (checked on the device before use).
+ * Errors: SQ_ERR_ARG, SQ_ERR_OOM, SQ_ERR_UNSUPPORTED, SQ_ERR_CUDA.  Synchronises `stream`.
+ */
+sq_status sq_moments_cols(sq_handle h, int K, int precision, const long long *d_cols, long long ncols,
+                          void *d_mu_out, void *stream);
 sq_status sq_observables(sq_handle h, double lambda_f, double kT, double N_e, const double *msum, const double *A,
                          double *d_rho, void *stream);
 
@@ -332,9 +367,9 @@ sq_status sq_density_vjp(sq_handle h, const double *d_rho_bar, double U_bar, int
  * Sec. 3 per cell): every cell's per-point recursion runs in ONE persistent kernel launch whose CTAs
  * take (cell, column-range) work items from a queue, followed by each cell's moment sums, Fermi
  * level, weights and density -- the whole sequence captured once into a CUDA graph and replayed.
- * In SQ_FP32, cells with cubic 21^3 or 25^3 cubes and the 12th-order stencil leave the queue and run
- * as one launch each of the FP32 slab kernel (the kernel sq_density uses for them), captured in the
- * same graph.
+ * In SQ_FP32, cells with cubic 21^3, 25^3 or 29^3 cubes and the 12th-order stencil leave the queue and
+ * run as one launch each of the kernel sq_density uses for them (the FP32 slab kernel for 21^3 and
+ * 25^3, the two-CTA cluster kernel for 29^3), captured in the same graph.
  *
  * sq_batch_create -- group built handles (cells may differ in grid, cube, atoms, K, kT, N_e; they must
  * share the FD order and the device).  Allocates every buffer the graph will use.
@@ -348,11 +383,15 @@ sq_status sq_batch_create(const sq_handle *cells, int ncells, const int *K, cons
                           int precision, int flags, sq_batch *out);
 
 /*
- * sq_batch_density -- run the batch.  The first call autotunes the recursion launch (vectors in shared
- * memory with 512 or 256 threads, or in global scratch; work items of 32 or 128 columns), timed on
- * a prefix of the work queue (256 columns per SM), then captures the graph; later calls with the same d_rho pointers
- * replay it (new pointers trigger a new capture).  Afterwards each handle holds its cell's results as
- * after sq_density, so sq_energy and sq_nonlocal_force apply per cell.
+ * sq_batch_density -- run the batch.  The first call autotunes the recursion launch of the work queue
+ * (vectors in shared memory with 512 or 256 threads, or in global scratch; work items of 32 or 128
+ * columns), timed on a prefix of the queue (256 columns per SM; skipped when every cell has its own
+ * launch), then captures the graph; later calls with the same d_rho pointers replay it (new pointers
+ * trigger a new capture).  The Fermi level of each cell is solved inside the graph by a fixed number
+ * of bisection launches (2 bracket checks and 94 halvings, enough to reach the last bit of any
+ * bracket within the spectral bounds' range of 2^94 ulps); a cell whose bisection has not closed by
+ * then is re-solved on the host-driven path of sq_density after the replay.  Afterwards each handle
+ * holds its cell's results as after sq_density, so sq_energy and sq_nonlocal_force apply per cell.
  *   d_rho[ncells]   device FP64 density outputs, one per cell (caller-owned)
  *   lambda_f        host [ncells] Fermi levels (may be NULL)
  * Errors: SQ_ERR_ARG, SQ_ERR_NO_BRACKET, SQ_ERR_NOT_FINITE, SQ_ERR_UNSUPPORTED, SQ_ERR_CUDA.

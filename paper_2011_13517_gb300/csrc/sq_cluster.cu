@@ -28,6 +28,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "sq_internal.h"
 #include "sq_slab_common.cuh"
 
@@ -305,6 +307,7 @@ __device__ int cluster_setup(const RecursionArgs<float> &args, const CSmem &S, l
         S.zlo[wd] = zl;
         S.zhi[wd] = zh;
     }
+    __syncthreads();   // tables and masks complete before any warp reads them
     *nfrc_out = nfrc;
     return nact;
 }
@@ -582,7 +585,8 @@ __global__ void __launch_bounds__(CGeo<NC, P>::NW * 32, 1) cluster_kernel(const 
                 }
             }
             // Y (arrive): this CTA's reads of v_k's buffer are done
-            asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+            __syncwarp();
+            auto y_token = cluster.barrier_arrive();
             // ---- KB term ----
             if (th.slab) {
                 for (int wd = 0; wd < W; wd++) {
@@ -593,7 +597,8 @@ __global__ void __launch_bounds__(CGeo<NC, P>::NW * 32, 1) cluster_kernel(const 
                 }
             }
             // Y (wait): both CTAs are done reading v_k's buffers
-            asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+            __syncwarp();
+            cluster.barrier_wait(std::move(y_token));
             // ---- v_{k+1} = ca Hhat v_k - cb v_{k-1}; v_k becomes v_{k-1} ----
 #pragma unroll
             for (int c = 0; c < NC; c++) {

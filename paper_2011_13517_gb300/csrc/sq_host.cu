@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "sq_gauss_rule.h"
 #include "sq_internal.h"
 
 using namespace sq;
@@ -93,6 +94,12 @@ struct sq_handle_s {
     // density state
     int have_density = 0, K = 0, precision = 0, have_force = 0;
     int have_moments = 0;           // moments of columns [q0, q1) are in d_mu, their sums in d_msum
+    int gauss = 0;                  // the last sq_density used Gauss (Lanczos) quadrature
+    double gU = 0, gS = 0;          // Gauss path: U and S at the last Fermi level
+    double *d_ab = nullptr;         // Gauss path: Lanczos coefficients [2K][N_d]
+    size_t ab_cap = 0;
+    double *d_gnode = nullptr;      // Gauss path: nodes [K][N_d] then weights [K][N_d]
+    size_t gnode_cap = 0;
     long long q0 = 0, q1 = 0;
     double kT = 0, N_e = 0, lam_f = 0;
     int M = 0;
@@ -550,6 +557,74 @@ __global__ void k_force(const double *A, const double *c, int K, int natom, int 
     }
 }
 
+// Gauss path (Sec. 2.2, Eqs. rhoq, uq, sq): rho(x_q) = 2 sum_k w_k g(lambda_k) / dV over the column's
+// nodes; U = 2 sum_q sum_k w lambda g and S = -2 sum_q sum_k w s(lambda) over all nodes (FP64,
+// deterministic two-stage sums).
+__global__ void k_gauss_density(const double *nodes, const double *weights, long long N_d, int K, double lam_f,
+                                double kT, double inv_dV, double *rho)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N_d; q += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < K; k++) s += weights[(size_t)k * N_d + q] * fermi_fn(nodes[(size_t)k * N_d + q], lam_f, kT);
+        rho[q] = 2.0 * s * inv_dV;
+    }
+}
+
+__device__ __forceinline__ double entropy_fn(double lam, double lam_f, double kT)
+{
+    // s(g) = g ln g + (1-g) ln(1-g) in the overflow-free form -(log1p(e^-|y|) + |y| g(|y|)), y = (lam - lam_f)/kT
+    const double y = fabs((lam - lam_f) / kT);
+    return -(log1p(exp(-y)) + y * fermi_fn(y, 0.0, 1.0));
+}
+
+__global__ void k_gauss_energy_partial(const double *nodes, const double *weights, long long n, double lam_f, double kT,
+                                       double *part)
+{
+    double u = 0.0, sv = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double l = nodes[i], w = weights[i];
+        u += w * l * fermi_fn(l, lam_f, kT);
+        sv += w * entropy_fn(l, lam_f, kT);
+    }
+    __shared__ double r0[32], r1[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        u += __shfl_xor_sync(0xffffffffu, u, o);
+        sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        r0[threadIdx.x >> 5] = u;
+        r1[threadIdx.x >> 5] = sv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            a += r0[w];
+            b += r1[w];
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void k_gauss_energy_final(const double *part, int nblk, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nblk; i++) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    out[0] = 2.0 * a;
+    out[1] = -2.0 * b;
+}
+
+__global__ void k_check_cols(const long long *cols, long long n, long long N_d, int *bad)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (cols[i] < 0 || cols[i] >= N_d) atomicExch(bad, 1);
+}
+
 // ------------------------------------------------------------------------------------------------
 // host helpers
 
@@ -802,6 +877,8 @@ extern "C" void sq_destroy(sq_handle h)
     cudaFree(h->d_coef);
     cudaFree(h->d_nodes);
     cudaFree(h->d_scratch);
+    cudaFree(h->d_ab);
+    cudaFree(h->d_gnode);
     for (int i = 0; i < 5; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     delete h;
@@ -848,7 +925,8 @@ static void fill_args(sq_handle h, int K, int want_force, RecursionArgs<T> &a)
 }
 
 template <typename T>
-static sq_status run_recursion(sq_handle h, int K, int want_force, long long q0, long long q1, cudaStream_t stream)
+static sq_status run_recursion(sq_handle h, int K, int want_force, long long q0, long long q1, cudaStream_t stream,
+                               const long long *cols = nullptr)
 {
     sq_status s;
     const size_t pad = (size_t)h->pn[0] * h->pn[1] * h->pn[2];
@@ -869,10 +947,11 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, long long q0,
     a.dpad = *dpad;
     a.q0 = q0;
     a.q1 = q1;
+    a.cols = cols;
 
     int dev_smem = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4) if (!cols) {
         // FP32 on a cubic 29^3 cube with the 12th-order stencil: the two-CTA cluster kernel, sized by
         // the largest number of atoms touching one cube
         if (h->natom > 0 && cluster_supported(h->nc, h->p)) {
@@ -960,6 +1039,7 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, long long q0,
     SQ_COUNT(1);
     SQ_CUDA(launch_recursion<T>(a, h->p, (int)grid, block, smem, stream));
     SQ_CUDA(cudaEventRecord(h->ev[1], stream));
+    if (cols) return SQ_OK;   // a column list: no range sums
     // moment sums
     dim3 g2(kSumBlocks, K + 1);
     SQ_COUNT(1);
@@ -1071,6 +1151,152 @@ static sq_status fermi_and_density(sq_handle h, double kT, double N_e, double *d
     return SQ_OK;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Gauss (Lanczos) quadrature path: Lanczos coefficients of every column, the Gauss rule of each
+// column's Jacobi matrix, the Fermi level over all nodes (Eq. Ne), rho, U and S.
+
+template <typename T>
+static sq_status run_lanczos(sq_handle h, int K, cudaStream_t stream)
+{
+    sq_status s;
+    const size_t pad = (size_t)h->pn[0] * h->pn[1] * h->pn[2];
+    T **dpad = nullptr;
+    if constexpr (sizeof(T) == 8) dpad = reinterpret_cast<T **>(&h->d_dpad64);
+    else dpad = reinterpret_cast<T **>(&h->d_dpad32);
+    if (!*dpad) {
+        size_t cap = 0;
+        if ((s = ensure(dpad, &cap, sizeof(T) * pad))) return s;
+    }
+    SQ_COUNT(1);
+    k_dpad<T><<<grid_for((long long)pad, 256, h->num_sms), 256, 0, stream>>>(
+        h->d_veff, h->n[0], h->n[1], h->n[2], h->m[0], h->m[1], h->m[2], h->kdiag, h->omega, h->tau, *dpad);
+    SQ_CUDA(cudaGetLastError());
+    RecursionArgs<T> a;
+    fill_args<T>(h, K, 0, a);
+    a.dpad = *dpad;
+    a.ab = h->d_ab;
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+    const size_t smem_vec = recursion_smem_bytes<T>(h->natom, h->nc, 1);
+    const size_t smem_glob = recursion_smem_bytes<T>(h->natom, h->nc, 0);
+    const int nseg = ((h->nc[0] + 7) / 8) * h->nc[1] * h->nc[2];
+    int block = 256;
+    if (sizeof(T) == 4 && smem_vec <= (size_t)dev_smem) {
+        a.vec_in_smem = 1;
+        block = nseg >= 1024 ? 512 : 256;
+    } else {
+        a.vec_in_smem = (smem_vec * 2 + 2048 <= (size_t)dev_smem) ? 1 : 0;
+    }
+    const size_t smem = a.vec_in_smem ? smem_vec : smem_glob;
+    if (smem > (size_t)dev_smem) return fail(SQ_ERR_UNSUPPORTED, "too many atoms for shared memory (%zu B)", smem);
+    const int per_sm = lanczos_blocks_per_sm<T>(h->p, block, smem, a.vec_in_smem);
+    if (per_sm < 1) return fail(SQ_ERR_UNSUPPORTED, "Lanczos kernel does not fit on an SM");
+    long long grid = (long long)per_sm * h->num_sms;
+    if (grid > h->N_d) grid = h->N_d;
+    if (!a.vec_in_smem) {
+        if ((s = ensure(&h->d_scratch, &h->scratch_cap, sizeof(T) * 2 * (size_t)h->nc3 * grid))) return s;
+        a.scratch = reinterpret_cast<T *>(h->d_scratch);
+    }
+    h->kernel_used = 3;
+    SQ_CUDA(cudaEventRecord(h->ev[0], stream));
+    SQ_COUNT(1);
+    SQ_CUDA(launch_lanczos<T>(a, h->p, (int)grid, block, smem, stream));
+    SQ_CUDA(cudaEventRecord(h->ev[1], stream));
+    return SQ_OK;
+}
+
+// Fermi level over the Gauss nodes (same bisection state machine as the Chebyshev path, with the
+// node energies and weights of all columns in place of the Chebyshev-Gauss nodes), then rho, U, S.
+static sq_status gauss_fermi_and_observables(sq_handle h, double kT, double N_e, double *d_rho, double *lambda_f,
+                                             cudaStream_t stream)
+{
+    const int K = h->K;
+    const long long nK = (long long)K * h->N_d;
+    const double *nodes = h->d_gnode, *weights = h->d_gnode + nK;
+    SQ_CUDA(cudaEventRecord(h->ev[3], stream));
+    FermiState *st = reinterpret_cast<FermiState *>(reinterpret_cast<char *>(h->d_small) + 256);
+    double *part = reinterpret_cast<double *>(reinterpret_cast<char *>(h->d_small) + 512);
+    FermiState init;
+    memset(&init, 0, sizeof(init));
+    init.lo = h->lmin;
+    init.hi = h->lmax_;
+    SQ_CUDA(cudaMemcpyAsync(st, &init, sizeof(init), cudaMemcpyHostToDevice, stream));
+    FermiState fin;
+    for (int round = 0; round < 16; round++) {
+        SQ_COUNT(16);
+        for (int i = 0; i < 16; i++)
+            k_fermi_step<<<kFermiBlocks, 256, 0, stream>>>(nodes, weights, (int)nK, kT, N_e, st, part);
+        SQ_CUDA(cudaGetLastError());
+        SQ_CUDA(cudaMemcpyAsync(&fin, st, sizeof(fin), cudaMemcpyDeviceToHost, stream));
+        SQ_CUDA(cudaStreamSynchronize(stream));
+        if (fin.phase >= 3) break;
+    }
+    if (fin.phase == 4)
+        return fail(SQ_ERR_NO_BRACKET, "N(lambda_min) = %.6g, N(lambda_max) = %.6g, N_e = %.6g", fin.N_lo, fin.N_hi, N_e);
+    if (fin.phase != 3) return fail(SQ_ERR_TIMEOUT, "bisection did not finish");
+    const double lf = fin.x;
+    if (!std::isfinite(lf)) return fail(SQ_ERR_NOT_FINITE, "Fermi level is not finite");
+    if (d_rho) {
+        SQ_COUNT(1);
+        k_gauss_density<<<grid_for(h->N_d, 256, h->num_sms), 256, 0, stream>>>(nodes, weights, h->N_d, K, lf, kT,
+                                                                             1.0 / h->dV, d_rho);
+        SQ_CUDA(cudaGetLastError());
+    }
+    double *epart = h->d_msum_part;   // 2 x kEnergyBlocks doubles (sized by sq_density)
+    double *eout = reinterpret_cast<double *>(h->d_small) + 4;
+    SQ_COUNT(2);
+    k_gauss_energy_partial<<<kSumBlocks, 256, 0, stream>>>(nodes, weights, nK, lf, kT, epart);
+    k_gauss_energy_final<<<1, 32, 0, stream>>>(epart, kSumBlocks, eout);
+    SQ_CUDA(cudaGetLastError());
+    double us[2];
+    SQ_CUDA(cudaMemcpyAsync(us, eout, sizeof(us), cudaMemcpyDeviceToHost, stream));
+    SQ_CUDA(cudaEventRecord(h->ev[4], stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    h->gU = us[0];
+    h->gS = us[1];
+    h->kT = kT;
+    h->N_e = N_e;
+    h->lam_f = lf;
+    if (lambda_f) *lambda_f = lf;
+    return SQ_OK;
+}
+
+static sq_status gauss_density(sq_handle h, int K, double kT, double N_e, int precision, double *d_rho,
+                               double *lambda_f, cudaStream_t stream)
+{
+    h->have_density = 0;
+    h->have_moments = 0;
+    sq_status s;
+    const size_t nK = (size_t)K * h->N_d;
+    if ((s = ensure(&h->d_ab, &h->ab_cap, sizeof(double) * 2 * nK))) return s;
+    if ((s = ensure(&h->d_gnode, &h->gnode_cap, sizeof(double) * 2 * nK))) return s;
+    if ((s = ensure(&h->d_msum_part, &h->part_cap, sizeof(double) * (size_t)(K + 1) * kSumBlocks))) return s;
+    h->precision = precision;
+    h->K = K;
+    s = precision == SQ_FP64 ? run_lanczos<double>(h, K, stream) : run_lanczos<float>(h, K, stream);
+    if (s) return s;
+    int *d_bad = reinterpret_cast<int *>(h->d_small);
+    SQ_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), stream));
+    SQ_COUNT(1);
+    SQ_CUDA(launch_gauss_rule(h->d_ab, h->N_d, 0, h->N_d, K, h->omega, h->tau, h->d_gnode, h->d_gnode + nK, d_bad,
+                              h->num_sms, stream));
+    SQ_CUDA(cudaEventRecord(h->ev[2], stream));
+    int bad = 0;
+    SQ_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    if (bad) return fail(SQ_ERR_NOT_FINITE, "a Jacobi eigensolve did not converge");
+    SQ_CUDA(cudaEventElapsedTime(&h->t_rec, h->ev[0], h->ev[1]));
+    SQ_CUDA(cudaEventElapsedTime(&h->t_msum, h->ev[1], h->ev[2]));
+    h->gauss = 1;
+    h->have_force = 0;
+    h->q0 = 0;
+    h->q1 = h->N_d;
+    if ((s = gauss_fermi_and_observables(h, kT, N_e, d_rho, lambda_f, stream))) return s;
+    SQ_CUDA(cudaEventElapsedTime(&h->t_fermi, h->ev[3], h->ev[4]));
+    h->have_density = 1;
+    return SQ_OK;
+}
+
 // Recursion over columns [q0, q1), moments into the handle's [K+1][N_d] buffer, and the moment sums of
 // those columns into h->d_msum (FP64).  Leaves the handle without a density (have_density = 0).
 static sq_status moments_stage(sq_handle h, int K, int precision, int want_force, long long q0, long long q1,
@@ -1122,7 +1348,10 @@ static sq_status check_density_args(sq_handle h, int K, double kT, double N_e, i
     if (!(kT > 0) || !std::isfinite(kT)) return fail(SQ_ERR_ARG, "kT = %g", kT);
     if (!(N_e > 0) || !(N_e < 2.0 * h->N_d)) return fail(SQ_ERR_ARG, "N_e = %g", N_e);
     if (precision != SQ_FP64 && precision != SQ_FP32) return fail(SQ_ERR_ARG, "precision %d", precision);
-    if (flags & ~SQ_WANT_FORCE) return fail(SQ_ERR_ARG, "flags %d", flags);
+    if (flags & ~(SQ_WANT_FORCE | SQ_GAUSS)) return fail(SQ_ERR_ARG, "flags %d", flags);
+    if ((flags & SQ_GAUSS) && (flags & SQ_WANT_FORCE))
+        return fail(SQ_ERR_ARG, "SQ_GAUSS gives rho, U and S; the force moments need the Chebyshev path");
+    if ((flags & SQ_GAUSS) && K > kGaussMaxK) return fail(SQ_ERR_ARG, "K = %d above the Gauss path's %d", K, kGaussMaxK);
     return SQ_OK;
 }
 
@@ -1134,6 +1363,8 @@ extern "C" sq_status sq_density(sq_handle h, int K, double kT, double N_e, int p
     sq_status s;
     if ((s = check_density_args(h, K, kT, N_e, precision, flags))) return s;
     cudaStream_t stream = (cudaStream_t)stream_;
+    if (flags & SQ_GAUSS) return gauss_density(h, K, kT, N_e, precision, d_rho, lambda_f, stream);
+    h->gauss = 0;
     const int want_force = (flags & SQ_WANT_FORCE) && h->natom > 0;
     if ((s = moments_stage(h, K, precision, want_force, 0, h->N_d, stream))) return s;
     if ((s = fermi_and_density(h, kT, N_e, d_rho, lambda_f, stream))) return s;
@@ -1150,6 +1381,7 @@ extern "C" sq_status sq_fermi_resolve(sq_handle h, double kT, double N_e, double
     if (!h->have_density || h->q0 != 0 || h->q1 != h->N_d)
         return fail(SQ_ERR_STATE, "sq_fermi_resolve needs a whole-grid sq_density first");
     if (!(kT > 0) || !(N_e > 0) || !(N_e < 2.0 * h->N_d)) return fail(SQ_ERR_ARG, "kT = %g, N_e = %g", kT, N_e);
+    if (h->gauss) return gauss_fermi_and_observables(h, kT, N_e, d_rho, lambda_f, (cudaStream_t)stream_);
     return fermi_and_density(h, kT, N_e, d_rho, lambda_f, (cudaStream_t)stream_);
 }
 
@@ -1171,11 +1403,64 @@ extern "C" sq_status sq_moments_range(sq_handle h, int K, int precision, int fla
     if (want_force && !A) return fail(SQ_ERR_ARG, "SQ_WANT_FORCE needs the force-moment output A");
     cudaStream_t stream = (cudaStream_t)stream_;
     sq_status s;
+    h->gauss = 0;
     if ((s = moments_stage(h, K, precision, want_force, q_begin, q_end, stream))) return s;
     SQ_CUDA(cudaMemcpyAsync(msum, h->d_msum, sizeof(double) * (K + 1), cudaMemcpyDeviceToHost, stream));
     if (want_force)
         SQ_CUDA(cudaMemcpyAsync(A, h->d_A, sizeof(double) * (size_t)(K + 1) * h->natom * h->nproj * 3,
                                 cudaMemcpyDeviceToHost, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    return SQ_OK;
+}
+
+template <typename T>
+__global__ void k_gather_mu(const T *mu, long long N_d, int K, const long long *cols, long long ncols, T *out)
+{
+    const long long tot = (long long)(K + 1) * ncols;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+        const long long k = t / ncols, i = t % ncols;
+        out[t] = mu[(size_t)k * N_d + cols[i]];
+    }
+}
+
+extern "C" sq_status sq_moments_cols(sq_handle h, int K, int precision, const long long *d_cols, long long ncols,
+                                     void *d_mu_out, void *stream_)
+{
+    g_last_error[0] = 0;
+    if (!h || !d_cols || !d_mu_out) return fail(SQ_ERR_ARG, "null argument");
+    if (K < 1 || K > 4096) return fail(SQ_ERR_ARG, "K = %d", K);
+    if (precision != SQ_FP64 && precision != SQ_FP32) return fail(SQ_ERR_ARG, "precision %d", precision);
+    if (ncols < 1 || ncols > h->N_d) return fail(SQ_ERR_ARG, "ncols = %lld", ncols);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    h->have_density = 0;
+    h->have_moments = 0;
+    h->gauss = 0;
+    sq_status s;
+    const size_t esz = precision == SQ_FP64 ? 8 : 4;
+    if ((s = ensure(&h->d_mu, &h->mu_bytes, esz * (size_t)(K + 1) * h->N_d))) return s;
+    h->precision = precision;
+    h->K = K;
+    // column indices are checked on the device against the grid before any use
+    int *d_bad = reinterpret_cast<int *>(h->d_small);
+    SQ_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), stream));
+    SQ_COUNT(1);
+    k_check_cols<<<grid_for(ncols, 256, h->num_sms), 256, 0, stream>>>(d_cols, ncols, h->N_d, d_bad);
+    SQ_CUDA(cudaGetLastError());
+    int bad = 0;
+    SQ_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    if (bad) return fail(SQ_ERR_ARG, "a column index is outside [0, N_d)");
+    s = precision == SQ_FP64 ? run_recursion<double>(h, K, 0, 0, ncols, stream, d_cols)
+                             : run_recursion<float>(h, K, 0, 0, ncols, stream, d_cols);
+    if (s) return s;
+    SQ_COUNT(1);
+    if (precision == SQ_FP64)
+        k_gather_mu<double><<<grid_for((K + 1) * ncols, 256, h->num_sms), 256, 0, stream>>>(
+            reinterpret_cast<const double *>(h->d_mu), h->N_d, K, d_cols, ncols, reinterpret_cast<double *>(d_mu_out));
+    else
+        k_gather_mu<float><<<grid_for((K + 1) * ncols, 256, h->num_sms), 256, 0, stream>>>(
+            reinterpret_cast<const float *>(h->d_mu), h->N_d, K, d_cols, ncols, reinterpret_cast<float *>(d_mu_out));
+    SQ_CUDA(cudaGetLastError());
     SQ_CUDA(cudaStreamSynchronize(stream));
     return SQ_OK;
 }
@@ -1321,11 +1606,39 @@ extern "C" sq_status sq_fermi_weights(double lambda_f, int K, double omega, doub
     return SQ_OK;
 }
 
+extern "C" sq_status sq_gauss_rule(const double *a, const double *b, int K, double omega, double tau, double *nodes,
+                                   double *weights)
+{
+    g_last_error[0] = 0;
+    if (!a || !b || !nodes || !weights) return fail(SQ_ERR_ARG, "null argument");
+    if (K < 1 || K > kGaussMaxK) return fail(SQ_ERR_ARG, "K = %d", K);
+    if (!(tau > 0) || !std::isfinite(omega) || !std::isfinite(tau)) return fail(SQ_ERR_ARG, "omega = %g, tau = %g", omega, tau);
+    double d[kGaussMaxK], e[kGaussMaxK], z[kGaussMaxK];
+    for (int k = 0; k < K; k++) {
+        if (!std::isfinite(a[k]) || !std::isfinite(b[k])) return fail(SQ_ERR_NOT_FINITE, "coefficient %d", k);
+        d[k] = a[k];
+        e[k] = b[k];
+    }
+    const int n = gauss_rule_inplace(d, e, z, K);
+    if (n < 0) return fail(SQ_ERR_NOT_FINITE, "the Jacobi eigensolve did not converge");
+    for (int k = 0; k < K; k++) {
+        nodes[k] = k < n ? tau * d[k] + omega : omega;
+        weights[k] = k < n ? z[k] * z[k] : 0.0;
+    }
+    return SQ_OK;
+}
+
 extern "C" sq_status sq_energy(sq_handle h, double *U, double *S, double *F, void *stream_)
 {
     g_last_error[0] = 0;
     if (!h) return fail(SQ_ERR_ARG, "null handle");
     if (!h->have_density) return fail(SQ_ERR_STATE, "sq_energy before sq_density");
+    if (h->gauss) {
+        if (U) *U = h->gU;
+        if (S) *S = h->gS;
+        if (F) *F = h->gU - h->kT * h->gS;
+        return SQ_OK;
+    }
     cudaStream_t stream = (cudaStream_t)stream_;
     double *d_out = reinterpret_cast<double *>(h->d_small) + 4;
     SQ_COUNT(1);
@@ -1366,7 +1679,7 @@ extern "C" sq_status sq_get_spectral_bounds(sq_handle h, double *lambda_min, dou
 extern "C" sq_status sq_get_moments(sq_handle h, int *K, int *precision, const void **d_mu, const double **d_msum)
 {
     if (!h) return fail(SQ_ERR_ARG, "null handle");
-    if (!h->have_density) return fail(SQ_ERR_STATE, "no moments yet");
+    if (!h->have_density || h->gauss) return fail(SQ_ERR_STATE, "no Chebyshev moments yet");
     if (K) *K = h->K;
     if (precision) *precision = h->precision;
     if (d_mu) *d_mu = h->d_mu;
@@ -1377,7 +1690,7 @@ extern "C" sq_status sq_get_moments(sq_handle h, int *K, int *precision, const v
 extern "C" sq_status sq_copy_moments(sq_handle h, void *d_mu, double *d_msum, void *stream_)
 {
     if (!h) return fail(SQ_ERR_ARG, "null handle");
-    if (!h->have_density) return fail(SQ_ERR_STATE, "no moments yet");
+    if (!h->have_density || h->gauss) return fail(SQ_ERR_STATE, "no Chebyshev moments yet");
     cudaStream_t stream = (cudaStream_t)stream_;
     const size_t esz = h->precision == SQ_FP64 ? 8 : 4;
     if (d_mu) SQ_CUDA(cudaMemcpyAsync(d_mu, h->d_mu, esz * (size_t)(h->K + 1) * h->N_d, cudaMemcpyDeviceToDevice, stream));
@@ -1400,6 +1713,7 @@ extern "C" const char *sq_kernel_name(sq_handle h)
     if (!h || !h->have_density) return "";
     if (h->kernel_used == 1) return h->nc[0] == 21 ? "slab_kernel<21,6>" : "slab_kernel<25,6>";
     if (h->kernel_used == 2) return "cluster_kernel<29,6>";
+    if (h->kernel_used == 3) return h->precision == SQ_FP64 ? "lanczos_kernel<double>" : "lanczos_kernel<float>";
     return h->precision == SQ_FP64 ? "recursion_kernel<double>" : "recursion_kernel<float>";
 }
 
@@ -2150,8 +2464,8 @@ extern "C" sq_status sq_density_vjp(sq_handle h, const double *d_rho_bar, double
 {
     g_last_error[0] = 0;
     if (!h || !d_rho_bar || !d_veff_bar) return fail(SQ_ERR_ARG, "null argument");
-    if (!h->have_density || h->q0 != 0 || h->q1 != h->N_d)
-        return fail(SQ_ERR_STATE, "sq_density_vjp needs a whole-grid sq_density first");
+    if (!h->have_density || h->q0 != 0 || h->q1 != h->N_d || h->gauss)
+        return fail(SQ_ERR_STATE, "sq_density_vjp needs a whole-grid Chebyshev sq_density first");
     if (checkpoint_k < 1 || checkpoint_k > h->K) return fail(SQ_ERR_ARG, "checkpoint interval %d (K = %d)", checkpoint_k, h->K);
     if (!std::isfinite(U_bar)) return fail(SQ_ERR_NOT_FINITE, "U_bar");
     cudaStream_t stream = (cudaStream_t)stream_;

@@ -23,6 +23,7 @@ struct RecursionArgs {
     int nc3;             // cube points
     long long N_d;       // grid points
     long long q0, q1;    // columns [q0, q1) of this launch (0 and N_d for the whole grid)
+    const long long *cols;   // generic kernel only: when set, launch index i in [q0, q1) is column cols[i]
     int K;               // polynomial order
     int natom;
     int nproj;           // 1 (s) or 4 (s + p)
@@ -47,6 +48,7 @@ struct RecursionArgs {
     // outputs
     T *mu;               // [K+1][N_d]
     double *A;           // [K+1][natom][nproj][3] (accumulated with atomics) or null
+    double *ab;          // Lanczos kernels: [2K][N_d], a_1..a_K then b_1..b_K of each column
     // vector storage
     T *scratch;          // [gridDim][2][nc3] when the vectors live in global memory
     int vec_in_smem;
@@ -87,6 +89,20 @@ template <typename T>
 cudaError_t launch_batch(const BatchLaunch<T> &b, int fd_half, cudaStream_t stream);
 template <typename T>
 int batch_blocks_per_sm(int fd_half, int block, size_t smem, int vec_in_smem);
+
+// Lanczos iteration (Eq. Lanczos) of every column in [q0, q1) with the generic column machinery,
+// writing args.ab; same launch configurations as launch_recursion.
+template <typename T>
+cudaError_t launch_lanczos(const RecursionArgs<T> &args, int fd_half, int grid, int block, size_t smem,
+                           cudaStream_t stream);
+template <typename T>
+int lanczos_blocks_per_sm(int fd_half, int block, size_t smem, int vec_in_smem);
+
+// Gauss nodes and weights of every column from its Lanczos coefficients (one thread per column):
+// nodes[k][N_d] = tau lambda_hat_k + omega, weights[k][N_d]; *bad is set when a column's tridiagonal
+// eigensolve did not converge.
+cudaError_t launch_gauss_rule(const double *ab, long long N_d, long long q0, long long q1, int K, double omega,
+                              double tau, double *nodes, double *weights, int *bad, int num_sms, cudaStream_t stream);
 
 // Launch the per-column recursion for all N_d columns.  Returns cudaSuccess or the launch error.
 template <typename T>

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libsq.so")
 SQ_FP64 = 0
 SQ_FP32 = 1
 SQ_WANT_FORCE = 1
+SQ_GAUSS = 2
 SQ_GRAD_ANALYTIC = 0
 SQ_GRAD_FD = 1
 
@@ -26,8 +27,9 @@ STATUS = {0: "SQ_OK", 1: "SQ_ERR_ARG", 2: "SQ_ERR_CUBE_EXCEEDS_BOX", 3: "SQ_ERR_
           4: "SQ_ERR_NOT_FINITE", 5: "SQ_ERR_CUDA", 6: "SQ_ERR_TIMEOUT", 7: "SQ_ERR_OOM",
           8: "SQ_ERR_STATE", 9: "SQ_ERR_UNSUPPORTED"}
 
-EXPORTS = ["sq_build_hamiltonian", "sq_density", "sq_fermi_level", "sq_fermi_weights", "sq_fermi_resolve",
-           "sq_moments_range", "sq_observables", "sq_energy", "sq_nonlocal_force",
+EXPORTS = ["sq_build_hamiltonian", "sq_density", "sq_fermi_level", "sq_fermi_weights", "sq_gauss_rule",
+           "sq_fermi_resolve",
+           "sq_moments_range", "sq_moments_cols", "sq_observables", "sq_energy", "sq_nonlocal_force",
            "sq_get_spectral_bounds", "sq_get_moments", "sq_copy_moments", "sq_get_cube", "sq_get_timing",
            "sq_kernel_launches", "sq_fma_throughput", "sq_moments_noalloc", "sq_batch_create", "sq_batch_density",
            "sq_batch_info", "sq_batch_destroy", "sq_density_vjp", "sq_kernel_name", "sq_destroy",
@@ -68,10 +70,12 @@ def lib():
         d = ctypes.c_double
         L.sq_fermi_level.argtypes = [dp, ctypes.c_int, d, d, d, d, d, d, dp]
         L.sq_fermi_weights.argtypes = [d, ctypes.c_int, d, d, d, dp, dp, dp]
+        L.sq_gauss_rule.argtypes = [dp, dp, ctypes.c_int, d, d, dp, dp]
         L.sq_fermi_resolve.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, dp, vp]
         L.sq_moments_range.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                                        ctypes.c_longlong, dp, dp, vp]
         L.sq_observables.argtypes = [vp, d, d, d, dp, dp, vp, vp]
+        L.sq_moments_cols.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_longlong, vp, vp]
         L.sq_fma_throughput.argtypes = [ctypes.c_int, dp, dp, vp]
         L.sq_energy.argtypes = [vp, dp, dp, dp, vp]
         L.sq_nonlocal_force.argtypes = [vp, vp, vp]
@@ -215,6 +219,17 @@ def sq_fermi_weights(lambda_f, K, omega, tau, kT):
     return tuple(out)
 
 
+def sq_gauss_rule(a, b, omega=0.0, tau=1.0):
+    """Host Gauss rule (nodes, weights) [K] of one grid point from its Lanczos coefficients a, b [K]."""
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    b = _host_f64(b, a.size)
+    nodes, weights = np.zeros(a.size), np.zeros(a.size)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().sq_gauss_rule(a.ctypes.data_as(dp), b.ctypes.data_as(dp), int(a.size), float(omega), float(tau),
+                               nodes.ctypes.data_as(dp), weights.ctypes.data_as(dp)))
+    return nodes, weights
+
+
 def sq_moments_range(h: Handle, K, precision, flags, q_begin, q_end, stream=None):
     """Recursion over columns [q_begin, q_end): returns (partial M_k [K+1], partial force moments
     [K+1, natom, nproj, 3] or None)."""
@@ -228,6 +243,14 @@ def sq_moments_range(h: Handle, K, precision, flags, q_begin, q_end, stream=None
                                   _stream(stream)))
     h.K, h.range = K, (int(q_begin), int(q_end))
     return msum, A
+
+
+def sq_moments_cols(h: Handle, K, precision, d_cols, d_mu_out, stream=None):
+    """Moments [K+1, ncols] of the listed grid points (d_cols: CUDA int64 tensor) into d_mu_out."""
+    n = int(d_cols.numel())
+    dt = torch.float64 if precision == SQ_FP64 else torch.float32
+    _check(lib().sq_moments_cols(h.ptr, int(K), int(precision), _dev_ptr(d_cols, torch.int64, numel=n), n,
+                                 _dev_ptr(d_mu_out, dt, numel=(int(K) + 1) * n), _stream(stream)))
 
 
 def sq_observables(h: Handle, lambda_f, kT, N_e, msum, A=None, d_rho=None, stream=None):

@@ -3,6 +3,7 @@
 Calls only oracle/ (and the seeded input generator).  Usage:
     python tests/golden/make_golden.py vacancy [--threads N]
     python tests/golden/make_golden.py batch_23          # cell 23 of the 32-cell batch workload
+    python tests/golden/make_golden.py vacancy_tangent   # oracle tangent of the vacancy cell (derivative test)
 The vacancy cell (118,944 grid points, K = 60, 25^3 cubes) takes about an hour of 8-core CPU time.
 """
 import argparse
@@ -29,6 +30,9 @@ def main():
     ap.add_argument("--refresh-digest", action="store_true",
                     help="only recompute the input digest field of an existing file")
     args = ap.parse_args()
+    if args.workload == "vacancy_tangent":
+        tangent_golden(args.threads)
+        return
     if args.workload.startswith("batch_"):
         cell = cells.batch_cells(32)[int(args.workload.split("_")[1])]
     else:
@@ -64,6 +68,44 @@ def main():
         "force": r["force"].tolist(),
     }
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{cell.name}.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(f"wrote {path} in {elapsed:.0f} s")
+
+
+def smooth_direction(cell, seed):
+    """Seeded smooth periodic field (6 Fourier modes, |k_i| <= 2), the perturbation direction dV."""
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(*[np.arange(cell.n[a]) / cell.n[a] for a in (2, 1, 0)], indexing="ij")
+    f = np.zeros(cell.n[::-1])
+    for _ in range(6):
+        k = rng.integers(-2, 3, size=3)
+        f += rng.standard_normal() * np.cos(2 * np.pi * (k[0] * x + k[1] * y + k[2] * z) + rng.uniform(0, 6.28))
+    return f.reshape(-1)
+
+
+def tangent_golden(threads):
+    """Forward-mode derivative of the vacancy cell's (rho, U) along a smooth direction dV (oracle
+    tangent: differentiated Chebyshev recursion plus the implicit Fermi-level term), contracted with a
+    seeded cotangent: D = <rho_bar, d rho> + U_bar dU.  A reverse-mode product must satisfy
+    <V_bar, dV> = D (the dot-product identity)."""
+    cell = cells.vacancy_cell()
+    bounds = oracle.spectral_bounds(cell)
+    rho_bar = np.random.default_rng(9).standard_normal(cell.N_d)
+    U_bar = 0.25
+    dV = smooth_direction(cell, 10)
+    t0 = time.time()
+    drho, dU, dlam, r = oracle.sq_tangent(cell, dV, bounds=bounds)
+    elapsed = time.time() - t0
+    idx = cells.sample_columns(cell, 64)
+    out = {"workload": "vacancy_95atom tangent", "digest": cell.digest(),
+           "note": "oracle forward-mode tangent (oracle.sq_tangent), written by tests/golden/make_golden.py",
+           "oracle_seconds": elapsed, "lmin": bounds[0], "lmax": bounds[1],
+           "rho_bar": "numpy default_rng(9).standard_normal(N_d)", "U_bar": U_bar,
+           "dV": "smooth_direction(cell, 10)",
+           "dot": float(np.dot(rho_bar, drho) + U_bar * dU), "dU": dU, "dlam_f": dlam,
+           "drho_idx": idx.tolist(), "drho": drho[idx].tolist()}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "vacancy_95atom_tangent.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print(f"wrote {path} in {elapsed:.0f} s")

@@ -7,11 +7,16 @@ tangent through the dot-product identity <rho_bar, d rho> + U_bar dU = <V_bar, d
 pointwise tangents, across checkpoint intervals, through the torch.autograd.Function, at the full
 size of the 95-atom vacancy cell (K = 60), and in FP32 on a 21^3-cube cell (the slab mapping)
 against the FP64 reverse mode."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 from oracle import oracle
 from paper_2011_13517_gb300 import cells
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def smooth_field(cell, seed):
@@ -127,22 +132,37 @@ def test_autograd_function_matches_vjp():
     assert abs(lhs - float(np.dot(g.cpu().numpy(), dV))) < 1e-9 * abs(lhs)
 
 
-@gpu
-def test_vjp_vacancy_cell_full_size():
-    """The 95-atom vacancy cell with K = 60 (the differentiation workload): FP32 reverse mode with
-    checkpoint intervals 1, 8 and 16 agree, and the FP64 reverse-mode directional derivative along a
-    smooth field matches central differences of the FP64 forward path (step 1e-4 Ha)."""
-    torch = _torch()
+@pytest.fixture(scope="module")
+def vacancy_vjp():
+    """Reverse-mode products of the 95-atom vacancy cell (K = 60, the differentiation workload) for the
+    seeded cotangent rho_bar ~ N(0, 1), U_bar = 0.25: FP32 with checkpoint intervals 1, 8, 16 and FP64
+    with interval 8, all with the oracle's spectral bounds held fixed."""
     from paper_2011_13517_gb300 import sq
+    _torch()
     c = cells.vacancy_cell()
     bounds = oracle.spectral_bounds(c)
-    rng = np.random.default_rng(9)
-    rho_bar = rng.standard_normal(c.N_d)
+    rho_bar = np.random.default_rng(9).standard_normal(c.N_d)
     U_bar = 0.25
     v32 = {kc: gpu_vjp(c, bounds, rho_bar, U_bar, kc, precision=sq.SQ_FP32) for kc in (1, 8, 16)}
+    v64 = gpu_vjp(c, bounds, rho_bar, U_bar, 8, precision=sq.SQ_FP64)
+    return dict(cell=c, bounds=bounds, rho_bar=rho_bar, U_bar=U_bar, v32=v32, v64=v64)
+
+
+@gpu
+def test_vjp_vacancy_checkpoint_intervals_agree(vacancy_vjp):
+    v32 = vacancy_vjp["v32"]
     scale = np.max(np.abs(v32[8]))
     for kc in (1, 16):
         np.testing.assert_allclose(v32[kc], v32[8], rtol=0, atol=1e-6 * scale)
+
+
+@gpu
+def test_vjp_vacancy_directional_finite_difference(vacancy_vjp):
+    """The FP64 reverse-mode directional derivative along a smooth field against central differences
+    of the FP64 forward path (step 1e-4 Ha); FP32 within 1e-3."""
+    from paper_2011_13517_gb300 import sq
+    c, bounds = vacancy_vjp["cell"], vacancy_vjp["bounds"]
+    rho_bar, U_bar = vacancy_vjp["rho_bar"], vacancy_vjp["U_bar"]
     dV = smooth_field(c, 10)
     eps = 1e-4
     vals = []
@@ -152,12 +172,85 @@ def test_vjp_vacancy_cell_full_size():
         r = sq.solve_cell(cc, sq.SQ_FP64, force=False, bounds=bounds)
         vals.append(float(np.dot(rho_bar, r["rho"]) + U_bar * r["U"]))
     fd = (vals[0] - vals[1]) / (2 * eps)
-    v64 = gpu_vjp(c, bounds, rho_bar, U_bar, 8, precision=sq.SQ_FP64)
-    ad64 = float(np.dot(v64, dV))
-    ad32 = float(np.dot(v32[8], dV))
+    ad64 = float(np.dot(vacancy_vjp["v64"], dV))
+    ad32 = float(np.dot(vacancy_vjp["v32"][8], dV))
     print("vacancy VJP directional derivative: FD", fd, "FP64", ad64, "FP32", ad32)
     assert abs(ad64 - fd) < 1e-6 * abs(fd)
     assert abs(ad32 - fd) < 1e-3 * abs(fd)
+
+
+@gpu
+def test_vjp_vacancy_matches_oracle_tangent(vacancy_vjp):
+    """Dot-product identity at full size against the oracle's forward-mode tangent (golden value from
+    tests/golden/make_golden.py vacancy_tangent): <V_bar, dV> = <rho_bar, d rho> + U_bar dU, FP64 with
+    checkpoint interval 8 within 1e-9, FP32 with intervals 1, 8 and 16 within 1e-4 (relative)."""
+    path = os.path.join(GOLDEN, "vacancy_95atom_tangent.json")
+    if not os.path.exists(path):
+        pytest.skip("golden file not generated")
+    g = json.load(open(path))
+    c = vacancy_vjp["cell"]
+    assert g["digest"] == c.digest() and abs(g["U_bar"] - vacancy_vjp["U_bar"]) == 0.0
+    assert abs(g["lmin"] - vacancy_vjp["bounds"][0]) < 1e-12 and abs(g["lmax"] - vacancy_vjp["bounds"][1]) < 1e-12
+    dV = smooth_field(c, 10)
+    d64 = float(np.dot(vacancy_vjp["v64"], dV))
+    print("tangent golden", g["dot"], "FP64 reverse", d64, {kc: float(np.dot(v, dV)) for kc, v in vacancy_vjp["v32"].items()})
+    assert abs(d64 - g["dot"]) < 1e-9 * abs(g["dot"])
+    for kc in (1, 8, 16):
+        assert abs(float(np.dot(vacancy_vjp["v32"][kc], dV)) - g["dot"]) < 1e-4 * abs(g["dot"])
+
+
+@gpu
+def test_vjp_vacancy_pointwise_finite_differences(vacancy_vjp):
+    """Central differences (step 1e-4 Ha) at 64 seeded grid points of the vacancy cell against the FP64
+    reverse-mode product there.  A change of V_eff at point p moves only the columns whose cube holds
+    p (the cube of columns around p), so each difference recomputes those 15,625 columns in FP64
+    (sq_moments_cols) and redoes the Fermi solve (Eq. Ne) and weights on the host (sq_fermi_level,
+    sq_fermi_weights) with the other columns' moments unchanged -- exact, not an approximation."""
+    torch = _torch()
+    from paper_2011_13517_gb300 import sq
+    c, bounds = vacancy_vjp["cell"], vacancy_vjp["bounds"]
+    rho_bar, U_bar, v64 = vacancy_vjp["rho_bar"], vacancy_vjp["U_bar"], vacancy_vjp["v64"]
+    lo, hi = bounds
+    omega, tau = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    K, dV = c.K, float(np.prod(c.h))
+    base = sq.solve_cell(c, sq.SQ_FP64, force=False, bounds=bounds)
+    mu0 = base["mu"]                              # [K+1, N_d]
+    M0 = mu0.sum(axis=1)
+    R0 = mu0 @ rho_bar
+    n = [int(x) for x in c.n]
+    m = [int(x) for x in c.m]
+    pts = np.random.default_rng(64).choice(c.N_d, size=64, replace=False)
+    eps = 1e-4
+    veff = torch.from_numpy(np.ascontiguousarray(c.veff.reshape(-1))).cuda()
+    out = torch.empty((K + 1) * int(np.prod(c.n_c)), dtype=torch.float64, device="cuda")
+    worst = 0.0
+    scale = float(np.max(np.abs(v64)))
+    for p in pts:
+        px, py, pz = p % n[0], (p // n[0]) % n[1], p // (n[0] * n[1])
+        gx = (px + np.arange(-m[0], m[0] + 1)) % n[0]
+        gy = (py + np.arange(-m[1], m[1] + 1)) % n[1]
+        gz = (pz + np.arange(-m[2], m[2] + 1)) % n[2]
+        cols = (gx[None, None, :] + n[0] * (gy[None, :, None] + n[1] * gz[:, None, None])).reshape(-1)
+        dcols = torch.from_numpy(cols.astype(np.int64)).cuda()
+        L = []
+        for sgn in (1.0, -1.0):
+            v = veff.clone()
+            v[int(p)] += sgn * eps
+            h = sq.build_for_cell(c, bounds=bounds, d_veff=v)
+            sq.sq_moments_cols(h, K, sq.SQ_FP64, dcols, out)
+            h.close()
+            mu = out.view(K + 1, cols.size).cpu().numpy()
+            dmu = mu - mu0[:, cols]
+            M = M0 + dmu.sum(axis=1)
+            R = R0 + dmu @ rho_bar[cols]
+            lam = sq.sq_fermi_level(M, K, omega, tau, lo, hi, c.kT, c.N_e)
+            cw, dw, _ = sq.sq_fermi_weights(lam, K, omega, tau, c.kT)
+            L.append(2.0 / dV * float(cw @ R) + U_bar * 2.0 * float(dw @ M))
+        fd = (L[0] - L[1]) / (2 * eps)
+        err = abs(fd - v64[p])
+        worst = max(worst, err / scale)
+        assert err < 1e-7 * scale + 1e-6 * abs(v64[p]), (int(p), fd, v64[p])
+    print("pointwise FD vs FP64 reverse mode at 64 points: max error / max |V_bar| =", worst)
 
 
 @gpu

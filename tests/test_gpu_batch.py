@@ -88,3 +88,62 @@ def test_batch_fp64_sampled_columns_match_oracle():
         ref = oracle.moments(c, omega, tau, cols=cols)
         np.testing.assert_allclose(mu.cpu().numpy()[:, cols].T, ref, rtol=0, atol=1e-12)
     b.close()
+
+
+def test_batch_32_cells_fp32_against_oracle():
+    """The 32-cell batch workload (48-288 sites, 0-2 vacancies, 0-2 Al, 21^3/25^3/29^3 cubes, K 40/60/80)
+    in FP32, one graph: for every cell, sampled moments against the oracle column by column (within
+    1e-6: K <= 80 steps of FP32 sums) and the sum rule; for the cells with oracle golden files (full
+    solves written by tests/golden/make_golden.py), lambda_f, U per atom, the forces and sampled rho
+    against the oracle within the paper's accuracy targets (1e-4 Ha/atom, 1e-4 Ha/bohr; Sec. 4) and
+    lambda_f within 1e-5 Ha."""
+    import json
+    import os
+    golden_dir = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    cs = cells.batch_cells(32)
+    bounds = []
+    for c in cs:
+        path = os.path.join(golden_dir, f"{c.name}.json")
+        if os.path.exists(path):
+            g = json.load(open(path))
+            assert g["digest"] == c.digest()
+            bounds.append((g["lmin"], g["lmax"]))
+        else:
+            bounds.append(oracle.spectral_bounds(c))
+    handles = [sq.build_for_cell(c, bounds=bd) for c, bd in zip(cs, bounds)]
+    b = sq.sq_batch_create(handles, [c.K for c in cs], [c.kT for c in cs], [c.N_e for c in cs], sq.SQ_FP32,
+                           sq.SQ_WANT_FORCE)
+    rhos = [torch.empty(c.N_d, dtype=torch.float64, device="cuda") for c in cs]
+    lam = sq.sq_batch_density(b, rhos)
+    worst = 0.0
+    ngolden = 0
+    for i, (h, c, bd) in enumerate(zip(handles, cs, bounds)):
+        mu, _ = sq.sq_copy_moments(h, c.N_d)
+        omega, tau = oracle.scale_shift(*bd)
+        cols = cells.sample_columns(c, 2, seed=100 + i)
+        ref = oracle.moments(c, omega, tau, cols=cols)
+        err = float(np.max(np.abs(mu.cpu().numpy()[:, cols].T - ref)))
+        worst = max(worst, err)
+        assert err < 1e-6, (c.name, err)
+        rho = rhos[i].cpu().numpy()
+        dV = float(np.prod(c.h))
+        assert abs(rho.sum() * dV - c.N_e) < 1e-9 * c.N_e
+        path = os.path.join(golden_dir, f"{c.name}.json")
+        if os.path.exists(path):
+            ngolden += 1
+            g = json.load(open(path))
+            U, S, F = sq.sq_energy(h)
+            f = torch.empty((c.natom, 3), dtype=torch.float64, device="cuda")
+            sq.sq_nonlocal_force(h, f)
+            idx = np.array(g["rho_idx"])
+            e = dict(dlam=abs(lam[i] - g["lam_f"]), dU_atom=abs(U - g["U"]) / c.natom,
+                     rho_rel=float(np.max(np.abs(rho[idx] - np.array(g["rho"]))) / np.max(np.abs(g["rho"]))),
+                     df=float(np.max(np.abs(f.cpu().numpy() - np.array(g["force"])))))
+            print(c.name, "FP32 batch vs oracle golden", e)
+            assert e["dlam"] < 1e-5 and e["dU_atom"] < 1e-4 and e["rho_rel"] < 1e-4 and e["df"] < 1e-4
+    print("32-cell batch: worst sampled-moment error", worst, "cells with golden files", ngolden)
+    info = sq.sq_batch_info(b)
+    assert info["graph_nodes"] > 0
+    b.close()
+    for h in handles:
+        h.close()

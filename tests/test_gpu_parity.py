@@ -169,7 +169,7 @@ def test_tiny_cell_fp32_within_stated_error(tiny):
     gpu = sq.solve_cell(c, sq.SQ_FP32, force=True, bounds=(ref["lmin"], ref["lmax"]))
     e = fp32_errors(gpu, ref, c)
     print("FP32 tiny errors", e)
-    assert e["mu_max"] < 2e-5
+    assert e["mu_max"] < 5e-7          # observed 1.1e-7
     assert e["rho_l1"] < 1e-5 and e["dU_per_atom"] < 1e-5 and e["dlam"] < 1e-5
     assert e["df_max"] < 1e-5
     assert abs(gpu["rho"].sum() * ref["dV"] - c.N_e) < 1e-9 * c.N_e
@@ -187,7 +187,7 @@ def test_vacancy_fp32_sampled_columns(vacancy):
     mu = oracle.moments(c, omega, tau, cols=cols)
     err = float(np.max(np.abs(gpu["mu"][:, cols].T - mu)))
     print("FP32 vacancy max moment error", err)
-    assert err < 5e-5
+    assert err < 5e-7                  # observed 8.5e-8 (K = 60)
     dV = float(np.prod(c.h))
     assert abs(gpu["rho"].sum() * dV - c.N_e) < 1e-9 * c.N_e
     path = os.path.join(GOLDEN, "vacancy_95atom.json")
@@ -216,7 +216,9 @@ def test_precision_cell_fp32_against_oracle_golden():
     omega, tau = oracle.scale_shift(g["lmin"], g["lmax"])
     cols = cells.sample_columns(c, 4)
     mu = oracle.moments(c, omega, tau, cols=cols)
-    assert float(np.max(np.abs(gpu["mu"][:, cols].T - mu))) < 5e-5
+    err = float(np.max(np.abs(gpu["mu"][:, cols].T - mu)))
+    print("FP32 precision-cell max moment error", err)
+    assert err < 1e-6                  # K = 80 steps of FP32 sums
     idx = np.array(g["rho_idx"])
     e = dict(dlam=abs(gpu["lam_f"] - g["lam_f"]), dU_atom=abs(gpu["U"] - g["U"]) / c.natom,
              rho_rel=float(np.max(np.abs(gpu["rho"][idx] - g["rho"])) / np.max(np.abs(g["rho"]))),
@@ -273,7 +275,7 @@ def test_fp32_21_cube_matches_oracle():
     omega, tau = oracle.scale_shift(lo, hi)
     cols = cells.sample_columns(c, 24)
     mu = oracle.moments(c, omega, tau, cols=cols)
-    assert float(np.max(np.abs(gpu["mu"][:, cols].T - mu))) < 2e-5
+    assert float(np.max(np.abs(gpu["mu"][:, cols].T - mu))) < 5e-7
     np.testing.assert_allclose(ref64["mu"][:, cols].T, mu, rtol=0, atol=1e-12)
     assert abs(gpu["lam_f"] - ref64["lam_f"]) < 1e-5
 

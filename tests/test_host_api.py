@@ -80,3 +80,41 @@ def test_binding_rejects_short_output_buffers():
         sq.sq_nonlocal_force(h, torch.zeros(11, dtype=torch.float64))
     with pytest.raises(ValueError, match="elements"):
         sq.sq_density_vjp(h, torch.zeros(50, dtype=torch.float64), 0.0, 1, torch.zeros(100, dtype=torch.float64))
+
+
+def test_host_gauss_rule_matches_scipy_eigh_tridiagonal():
+    """sq_gauss_rule (the routine the GPU runs per column) against scipy's tridiagonal eigensolver:
+    nodes = eigenvalues of the Jacobi matrix, weights = squared first eigenvector components."""
+    from scipy.linalg import eigh_tridiagonal
+    rng = np.random.default_rng(3)
+    for K in (1, 2, 5, 40, 80, 256):
+        a = rng.uniform(-0.9, 0.9, K)
+        b = rng.uniform(0.05, 0.5, K)
+        nodes, w = sq.sq_gauss_rule(a, b, omega=0.5, tau=2.0)
+        lam, vec = eigh_tridiagonal(a, b[:K - 1]) if K > 1 else (a.copy(), np.ones((1, 1)))
+        order = np.argsort(nodes)
+        np.testing.assert_allclose(nodes[order], 2.0 * lam + 0.5, rtol=0, atol=1e-13 * K)
+        np.testing.assert_allclose(w[order], vec[0] ** 2, rtol=0, atol=1e-13 * K)
+        assert abs(w.sum() - 1.0) < 1e-13
+
+
+def test_host_gauss_rule_matches_oracle_lanczos_rule(tiny_ref):
+    """The same rule on Lanczos coefficients of real columns (tiny cell): equal to the oracle's."""
+    c, ref = tiny_ref
+    cols = np.array([0, 100, 2000])
+    a, b = oracle.lanczos(c, ref["omega"], ref["tau"], cols=cols)
+    on, ow = oracle.gauss_rule(a, b, ref["omega"], ref["tau"])
+    for i in range(cols.size):
+        nodes, w = sq.sq_gauss_rule(a[i], b[i], ref["omega"], ref["tau"])
+        o1, o2 = np.argsort(nodes), np.argsort(on[i])
+        np.testing.assert_allclose(nodes[o1], on[i][o2], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(w[o1], ow[i][o2], rtol=0, atol=1e-12)
+
+
+def test_host_gauss_rule_cuts_at_an_exhausted_krylov_space():
+    a = np.array([0.1, -0.2, 0.3, 0.0])
+    b = np.array([0.5, 0.0, 0.7, 0.0])
+    nodes, w = sq.sq_gauss_rule(a, b)
+    assert abs(w.sum() - 1.0) < 1e-14 and w[2] == 0.0 and w[3] == 0.0
+    lam = np.linalg.eigvalsh(np.array([[0.1, 0.5], [0.5, -0.2]]))
+    np.testing.assert_allclose(np.sort(nodes[:2]), lam, rtol=0, atol=1e-14)

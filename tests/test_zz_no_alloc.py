@@ -13,9 +13,9 @@ pytestmark = pytest.mark.gpu
 
 from paper_2011_13517_gb300 import cells, sq  # noqa: E402
 
-# the moment tolerances of the parity tests (|mu_k| <= 1): FP64 1e-12; FP32 5e-5 (sq_density may run
-# a different FP32 kernel, so the two FP32 results agree only to FP32 rounding)
-ATOL = {sq.SQ_FP64: 1e-12, sq.SQ_FP32: 5e-5}
+# the moment tolerances of the parity tests (|mu_k| <= 1): FP64 1e-12; FP32 1e-6 (sq_density may run
+# a different FP32 kernel, so the two FP32 results agree only to FP32 rounding, ~1e-7)
+ATOL = {sq.SQ_FP64: 1e-12, sq.SQ_FP32: 1e-6}
 
 
 @pytest.fixture(scope="module", autouse=True)
