@@ -5,23 +5,26 @@
 // Hamiltonian, with the Kleinman-Bylander term and the force moments of Eq. NLforceSQ).  A 29^3
 // cube does not fit the one-CTA slab mapping: its two FP32 vectors alone take 190 KB of shared
 // memory, and 29 warps leave 64 registers per thread for two 29-point pencils.  Here the cube's
-// y-slabs are split between the two CTAs of a cluster (rank 0: slabs 0..14, rank 1: 15..28):
-//   - warp w of rank r owns y-slab b = 15 r + w; lane l holds x position a = l (lanes 29..31 are
-//     zero), and the z-pencil of v_k stays in registers (128 registers per thread: one 480-thread
-//     CTA per SM);
-//   - each CTA keeps in shared memory its own slabs of v_k plus the 6 slabs next to the split that
-//     belong to the partner (the y reach of the stencil); after every step each CTA writes its 6
+// y-slabs are split between the two CTAs of a cluster (rank 0: slabs 0..14, rank 1: 15..28), and
+// each slab's z range between two warps of its CTA (z 0..14 and z 15..28):
+//   - warp 2s + h of rank r owns y-slab b = 15 r + s and z-half h; lane l holds x position a = l
+//     (lanes 29..31 are zero), and the warp's 15-point z-pencil of v_k stays in registers (30 warps,
+//     64 registers per thread, one 960-thread CTA per SM); v_{k-1} waits in per-CTA global scratch
+//     (L2-resident), read and written once per step;
+//   - each CTA keeps in shared memory its own slabs of v_k (all z) plus the 6 slabs next to the split
+//     that belong to the partner (the y reach of the stencil); after every step each CTA writes its
 //     boundary slabs of v_{k+1} straight into the partner's buffer (distributed shared memory);
-//   - v_{k-1} lives in registers; x neighbours come from predicated warp shuffles, y neighbours
-//     from the shared buffer, z neighbours from registers;
-//   - projector contractions chi^T v as in the slab kernel (two atoms per pass, z-half classes,
-//     transposed butterflies, per-slab slots, fixed-order sums); each CTA sums its own slabs and
-//     writes its partial into both CTAs, and both form the same total in the same order;
-//   - force moments: each CTA adds its slabs' partial sums to A with FP64 atomics;
+//   - x neighbours come from predicated warp shuffles, y neighbours from the shared buffer, z
+//     neighbours from registers, or from the shared buffer across the z split;
+//   - projector contractions chi^T v as in the slab kernel (two atoms per pass, transposed
+//     butterflies, per-(slab, z-half) slots, fixed-order sums) over each warp's z half, skipping the
+//     atoms whose support lies in the other half; each CTA sums its own slots and writes its partial
+//     into both CTAs, and both form the same total in the same order;
+//   - force moments: each CTA adds its slots' partial sums to A with FP64 atomics;
 //   - two cluster barriers per step: X after the partial dots are exchanged (it also publishes
-//     the halo slabs written in the previous step), and Y between the last read of v_k's buffer
-//     (the local stencil) and the first write of v_{k+1}, split into arrive/wait around the
-//     KB update so its latency overlaps that work.
+//     the halo slabs and the other z half written in the previous step), and Y between the last
+//     read of v_k's buffer (the local stencil) and the first write of v_{k+1}, split into
+//     arrive/wait around the KB update so its latency overlaps that work.
 // The barriers are hardware cluster barriers reached the same number of times by both CTAs (both
 // take identical control flow: the column sequence, atom lists and K are shared), so no wait is open
 // ended.  No TMA multicast is used.
@@ -43,34 +46,40 @@ using namespace slabdev;
 template <int NC, int P>
 struct CGeo {
     static constexpr int NB0 = (NC + 1) / 2;              // y-slabs of rank 0 (rank 1 owns NC - NB0)
-    static constexpr int NW = NB0;                        // warps per CTA
+    static constexpr int NW = 2 * NB0;                    // warps per CTA: two z halves per slab
     static constexpr int NR = NB0 + P;                    // rows of the shared vector buffer
     static constexpr int HB = NB0 - P;                    // slab held in row 0 of rank 1's buffer
-    static constexpr int NZ = (NC + 1) & ~1;              // z-table entries per atom (even)
-    static constexpr int HALF = ((NC - 1) / 2) & ~1;      // even split point of the z range
-    static_assert(NC <= 32 && NC - NB0 + P <= NR, "layout");
+    static constexpr int ZS = (NC + 1) / 2;               // z split: half 0 holds z < ZS, half 1 the rest
+    static constexpr int ZL = ZS;                         // pencil registers per thread
+    static constexpr int NZP = (ZL + 1) / 2;              // float4 z-table entries per atom and half
+    static constexpr int SCR = NC * NB0 * 32;             // floats of v_{k-1} scratch per CTA
+    static_assert(NC <= 32 && NC - NB0 + P <= NR && 2 * ZS >= NC, "layout");
+};
+template <int NC, int P, int H>
+struct ZHalf {
+    static constexpr int Z0 = H * CGeo<NC, P>::ZS;                         // first z of the half
+    static constexpr int LEN = H ? NC - CGeo<NC, P>::ZS : CGeo<NC, P>::ZS;  // z points of the half
 };
 
 struct CSmem {
     float *U;          // [NC z][NR rows][NC x]: own slabs of v_k plus the partner's P boundary slabs
     float2 *tx;        // [amax][NC]   (g, hp) along x
     float2 *ty;        // [amax][NB0]  (g, hp) along y, own slabs
-    float4 *tz;        // [amax][NZ/2] (g[c], hp[c], g[c+1], hp[c+1]) along z
+    float4 *tz;        // [2][amax][NZP] per z half: (g[z], hp[z], g[z+1], hp[z+1]) from the half's first z
     float2 *fx;        // [fmax][NC]   (g', hp') of force atoms
     float2 *fy;        // [fmax][NB0]
-    float4 *fz;        // [fmax][NZ/2]
-    float *slot;       // [NB0][amax][4]
-    float *fslot;      // [NB0][fmax][12]
+    float4 *fz;        // [2][fmax][NZP]
+    float *slot;       // [NB0][2][amax][4] per (slab, z half)
+    float *fslot;      // [NB0][2][fmax][12]
     float *part;       // [2][amax][4]: partial dots of rank 0 and rank 1 (each written by its rank)
     float *sd;         // [amax][4]: total dots
     SlabRec *rec;      // [amax]
     double *chiq;      // [fmax][4]
     int *ftl;          // [fmax]
     unsigned *ymask;   // [NB0][W] own slabs
+    unsigned *zmask;   // [2][W]: atoms whose z support meets half h
     unsigned *fbits;   // [W]
-    unsigned *zlo;     // [W]
-    unsigned *zhi;     // [W]
-    float4 *zero;      // [NZ/2]
+    float4 *zero;      // [NZP]
     int *scan;         // [40]
 };
 
@@ -91,22 +100,21 @@ __host__ __device__ inline size_t cluster_layout(unsigned char *base, int amax, 
     p = take(sizeof(float) * (size_t)NC * G::NR * NC);         if (s) s->U = (float *)p;
     p = take(sizeof(float2) * (size_t)amax * NC);              if (s) s->tx = (float2 *)p;
     p = take(sizeof(float2) * (size_t)amax * G::NB0);          if (s) s->ty = (float2 *)p;
-    p = take(sizeof(float2) * (size_t)amax * G::NZ);           if (s) s->tz = (float4 *)p;
+    p = take(sizeof(float4) * (size_t)2 * amax * G::NZP);      if (s) s->tz = (float4 *)p;
     p = take(sizeof(float2) * (size_t)fmax * NC);              if (s) s->fx = (float2 *)p;
     p = take(sizeof(float2) * (size_t)fmax * G::NB0);          if (s) s->fy = (float2 *)p;
-    p = take(sizeof(float2) * (size_t)fmax * G::NZ);           if (s) s->fz = (float4 *)p;
-    p = take(sizeof(float) * (size_t)G::NB0 * amax * 4);       if (s) s->slot = (float *)p;
-    p = take(sizeof(float) * (size_t)G::NB0 * fmax * 12);      if (s) s->fslot = (float *)p;
+    p = take(sizeof(float4) * (size_t)2 * fmax * G::NZP);      if (s) s->fz = (float4 *)p;
+    p = take(sizeof(float) * (size_t)G::NB0 * 2 * amax * 4);   if (s) s->slot = (float *)p;
+    p = take(sizeof(float) * (size_t)G::NB0 * 2 * fmax * 12);  if (s) s->fslot = (float *)p;
     p = take(sizeof(float) * (size_t)2 * amax * 4);            if (s) s->part = (float *)p;
     p = take(sizeof(float) * (size_t)amax * 4);                if (s) s->sd = (float *)p;
     p = take(sizeof(SlabRec) * (size_t)amax);                  if (s) s->rec = (SlabRec *)p;
     p = take(sizeof(double) * (size_t)fmax * 4);               if (s) s->chiq = (double *)p;
     p = take(sizeof(int) * (size_t)fmax);                      if (s) s->ftl = (int *)p;
     p = take(sizeof(unsigned) * (size_t)G::NB0 * W);           if (s) s->ymask = (unsigned *)p;
+    p = take(sizeof(unsigned) * (size_t)2 * W);                if (s) s->zmask = (unsigned *)p;
     p = take(sizeof(unsigned) * (size_t)W);                    if (s) s->fbits = (unsigned *)p;
-    p = take(sizeof(unsigned) * (size_t)W);                    if (s) s->zlo = (unsigned *)p;
-    p = take(sizeof(unsigned) * (size_t)W);                    if (s) s->zhi = (unsigned *)p;
-    p = take(sizeof(float4) * (size_t)(G::NZ / 2));            if (s) s->zero = (float4 *)p;
+    p = take(sizeof(float4) * (size_t)G::NZP);                 if (s) s->zero = (float4 *)p;
     p = take(sizeof(int) * 40);                                if (s) s->scan = (int *)p;
     return off;
 }
@@ -115,7 +123,9 @@ __host__ __device__ inline size_t cluster_layout(unsigned char *base, int amax, 
 template <int NC, int P>
 struct CThread {
     int lane, w, rank;
-    int b;            // global y-slab of this warp (NC for rank 1's spare warp when NC is odd)
+    int bl;           // local y-slab of this warp (0 .. NB0-1)
+    int zh;           // z half of this warp
+    int b;            // global y-slab (NC for rank 1's spare slab when NC is odd)
     int a;            // x position (= lane)
     bool slab;        // the warp owns a slab
     bool live;        // the thread holds a cube pencil
@@ -129,7 +139,9 @@ struct CThread {
         rank = rank_;
         lane = threadIdx.x & 31;
         w = threadIdx.x >> 5;
-        b = rank * G::NB0 + w;
+        bl = w >> 1;
+        zh = w & 1;
+        b = rank * G::NB0 + bl;
         a = lane;
         slab = b < NC;
         live = slab && a < NC;
@@ -161,13 +173,14 @@ __device__ __forceinline__ float xpair(float t, float x, int j, float wgt)
 }
 
 // Per-column set-up (same rules as slab_setup): ordered active atoms, window tables (y tables and
-// masks for this CTA's slabs), force atoms and their tables.  Both CTAs compute the same lists.
+// masks for this CTA's slabs, z tables per z half), force atoms and their tables.  Both CTAs compute
+// the same lists.  Ends with a CTA barrier: the tables and masks are complete when it returns.
 template <int NC, int P>
 __device__ int cluster_setup(const RecursionArgs<float> &args, const CSmem &S, long long q, int amax, int fmax,
                              int *err, int qa[3], int *nfrc_out, int rank)
 {
     using G = CGeo<NC, P>;
-    constexpr int NZ = G::NZ, NB0 = G::NB0, kHalf = G::HALF;
+    constexpr int NB0 = G::NB0, NZP = G::NZP, ZS = G::ZS;
     const int NTH = blockDim.x;
     const int W = (amax + 31) / 32;
     const int natom = args.natom;
@@ -205,6 +218,12 @@ __device__ int cluster_setup(const RecursionArgs<float> &args, const CSmem &S, l
         return -1;
     }
     __syncthreads();
+    // z factor (g, hp) of atom J at cube z, or zeros outside the cube
+    auto zfac = [&](int J, int z, int f0) {
+        if (z >= NC) return make_float2(0.f, 0.f);
+        const float *f2 = args.fac + (size_t)J * args.fac_stride + args.fac_off[2] + wstart[2] + z;
+        return make_float2(f2[f0 * args.n[2]], f2[(f0 + 2) * args.n[2]]);
+    };
     for (int it = threadIdx.x; it < nact * NC; it += NTH) {
         const int o = it % NC, t = it / NC;
         const float *f0 = args.fac + (size_t)S.rec[t].J * args.fac_stride + args.fac_off[0] + wstart[0] + o;
@@ -219,14 +238,13 @@ __device__ int cluster_setup(const RecursionArgs<float> &args, const CSmem &S, l
         }
         S.ty[it] = v;
     }
-    for (int it = threadIdx.x; it < nact * NZ; it += NTH) {
-        const int o = it % NZ, t = it / NZ;
-        float2 v = make_float2(0.f, 0.f);
-        if (o < NC) {
-            const float *f2 = args.fac + (size_t)S.rec[t].J * args.fac_stride + args.fac_off[2] + wstart[2] + o;
-            v = make_float2(f2[0], f2[2 * args.n[2]]);
-        }
-        reinterpret_cast<float2 *>(S.tz)[it] = v;
+    for (int it = threadIdx.x; it < 2 * nact * NZP; it += NTH) {
+        const int i = it % NZP, t = (it / NZP) % nact, h = it / (NZP * nact);
+        const int z = h * ZS + 2 * i;
+        const int zend = h ? NC : ZS;
+        const float2 u = z < zend ? zfac(S.rec[t].J, z, 0) : make_float2(0.f, 0.f);
+        const float2 v = z + 1 < zend ? zfac(S.rec[t].J, z + 1, 0) : make_float2(0.f, 0.f);
+        S.tz[((size_t)h * amax + t) * NZP + i] = make_float4(u.x, u.y, v.x, v.y);
     }
     int nfrc = 0;
     if (args.want_force) {
@@ -275,15 +293,14 @@ __device__ int cluster_setup(const RecursionArgs<float> &args, const CSmem &S, l
             }
             S.fy[it] = v;
         }
-        for (int it = threadIdx.x; it < nfrc * NZ; it += NTH) {
-            const int o = it % NZ, fi = it / NZ;
-            float2 v = make_float2(0.f, 0.f);
-            if (o < NC) {
-                const float *f2 = args.fac + (size_t)S.rec[S.ftl[fi]].J * args.fac_stride + args.fac_off[2] +
-                                  wstart[2] + o;
-                v = make_float2(f2[4 * args.n[2]], f2[6 * args.n[2]]);
-            }
-            reinterpret_cast<float2 *>(S.fz)[it] = v;
+        for (int it = threadIdx.x; it < 2 * nfrc * NZP; it += NTH) {
+            const int i = it % NZP, fi = (it / NZP) % nfrc, h = it / (NZP * nfrc);
+            const int z = h * ZS + 2 * i;
+            const int zend = h ? NC : ZS;
+            const int J = S.rec[S.ftl[fi]].J;
+            const float2 u = z < zend ? zfac(J, z, 4) : make_float2(0.f, 0.f);
+            const float2 v = z + 1 < zend ? zfac(J, z + 1, 4) : make_float2(0.f, 0.f);
+            S.fz[((size_t)h * fmax + fi) * NZP + i] = make_float4(u.x, u.y, v.x, v.y);
         }
     }
     for (int it = threadIdx.x; it < NB0 * W; it += NTH) {
@@ -296,46 +313,48 @@ __device__ int cluster_setup(const RecursionArgs<float> &args, const CSmem &S, l
         S.ymask[it] = msk;
     }
     for (int wd = threadIdx.x; wd < W; wd += NTH) {
-        unsigned fb = 0u, zl = 0u, zh = 0u;
+        unsigned fb = 0u, z0 = 0u, z1 = 0u;
         for (int t = 32 * wd; t < min(nact, 32 * wd + 32); t++) {
             const unsigned bit = 1u << (t - 32 * wd);
             if (S.rec[t].fidx >= 0) fb |= bit;
-            if (S.rec[t].hi[2] <= kHalf) zl |= bit;
-            else if (S.rec[t].lo[2] >= kHalf) zh |= bit;
+            if (S.rec[t].lo[2] < ZS) z0 |= bit;
+            if (S.rec[t].hi[2] >= ZS) z1 |= bit;
         }
         S.fbits[wd] = fb;
-        S.zlo[wd] = zl;
-        S.zhi[wd] = zh;
+        S.zmask[wd] = z0;
+        S.zmask[W + wd] = z1;
     }
     __syncthreads();   // tables and masks complete before any warp reads them
     *nfrc_out = nfrc;
     return nact;
 }
 
-// Projector contractions of two atoms per pass over z in [C0, C1), into this warp's slab slots.
-template <int NC, int P, int C0, int C1>
-__device__ __forceinline__ void cl_dots_pairs(unsigned msk, int wd, const CSmem &S, const float (&vz)[NC], int bl,
-                                              int a, bool live, int lane, int amax)
+// Projector contractions of two atoms per pass over the warp's z half, into its (slab, half) slots.
+template <int NC, int P, int H>
+__device__ __forceinline__ void cl_dots_pairs(unsigned msk, int wd, const CSmem &S, const float (&vz)[CGeo<NC, P>::ZL],
+                                              int bl, int a, bool live, int lane, int amax)
 {
-    constexpr int NZ = CGeo<NC, P>::NZ, NB0 = CGeo<NC, P>::NB0;
+    constexpr int NZP = CGeo<NC, P>::NZP, NB0 = CGeo<NC, P>::NB0, LEN = ZHalf<NC, P, H>::LEN;
+    const float4 *tzh = S.tz + (size_t)H * amax * NZP;
+    float *slot = S.slot + ((size_t)bl * 2 + H) * amax * 4;
     while (msk) {
         const int t0 = 32 * wd + __ffs(msk) - 1;
         msk &= msk - 1u;
         const bool two = msk != 0u;
         const int t1 = two ? 32 * wd + __ffs(msk) - 1 : t0;
         msk &= msk - 1u;
-        const float4 *z0 = S.tz + t0 * (NZ / 2);
-        const float4 *z1 = two ? S.tz + t1 * (NZ / 2) : S.zero;
+        const float4 *z0 = tzh + t0 * NZP;
+        const float4 *z1 = two ? tzh + t1 * NZP : S.zero;
         float G0a = 0.f, H0a = 0.f, G0b = 0.f, H0b = 0.f;
         float G1a = 0.f, H1a = 0.f, G1b = 0.f, H1b = 0.f;
 #pragma unroll
-        for (int c = C0; c < C1; c += 2) {
+        for (int c = 0; c < LEN; c += 2) {
             const float4 p0 = z0[c >> 1], p1 = z1[c >> 1];
             G0a += p0.x * vz[c];
             H0a += p0.y * vz[c];
             G1a += p1.x * vz[c];
             H1a += p1.y * vz[c];
-            if (c + 1 < NC) {
+            if (c + 1 < LEN) {
                 G0b += p0.z * vz[c + 1];
                 H0b += p0.w * vz[c + 1];
                 G1b += p1.z * vz[c + 1];
@@ -352,17 +371,18 @@ __device__ __forceinline__ void cl_dots_pairs(unsigned msk, int wd, const CSmem 
             const int t = idx < 4 ? t0 : t1;
             const int comp = idx & 3;
             const float2 yv = S.ty[t * NB0 + bl];
-            S.slot[((size_t)bl * amax + t) * 4 + (comp == 2 ? 3 : comp == 3 ? 2 : comp)] = (comp == 3 ? yv.y : yv.x) * red;
+            slot[t * 4 + (comp == 2 ? 3 : comp == 3 ? 2 : comp)] = (comp == 3 ? yv.y : yv.x) * red;
         }
     }
 }
 
-// KB update of two atoms per pass over z in [C0, C1): w += kappa_l chi (chi^T v) from the total dots.
-template <int NC, int P, int C0, int C1>
-__device__ __forceinline__ void cl_update_pairs(unsigned msk, int wd, const CSmem &S, float (&w)[NC], int bl, int a,
-                                                bool live, float kap0, float kap1)
+// KB update of two atoms per pass over the warp's z half: w += kappa_l chi (chi^T v) from the total dots.
+template <int NC, int P, int H>
+__device__ __forceinline__ void cl_update_pairs(unsigned msk, int wd, const CSmem &S, float (&w)[CGeo<NC, P>::ZL],
+                                                int bl, int a, bool live, float kap0, float kap1, int amax)
 {
-    constexpr int NZ = CGeo<NC, P>::NZ, NB0 = CGeo<NC, P>::NB0;
+    constexpr int NZP = CGeo<NC, P>::NZP, NB0 = CGeo<NC, P>::NB0, LEN = ZHalf<NC, P, H>::LEN;
+    const float4 *tzh = S.tz + (size_t)H * amax * NZP;
     while (msk) {
         const int t0 = 32 * wd + __ffs(msk) - 1;
         msk &= msk - 1u;
@@ -382,102 +402,114 @@ __device__ __forceinline__ void cl_update_pairs(unsigned msk, int wd, const CSme
             A1[i] = xv.x * Pv + xv.y * Rv;
             A2[i] = xv.x * Qv;
         }
-        const float4 *z0 = S.tz + t0 * (NZ / 2);
-        const float4 *z1 = two ? S.tz + t1 * (NZ / 2) : S.zero;
+        const float4 *z0 = tzh + t0 * NZP;
+        const float4 *z1 = two ? tzh + t1 * NZP : S.zero;
 #pragma unroll
-        for (int c = C0; c < C1; c += 2) {
+        for (int c = 0; c < LEN; c += 2) {
             const float4 p0 = z0[c >> 1], p1 = z1[c >> 1];
             w[c] += p0.x * A1[0] + p0.y * A2[0] + p1.x * A1[1] + p1.y * A2[1];
-            if (c + 1 < NC) w[c + 1] += p0.z * A1[0] + p0.w * A2[0] + p1.z * A1[1] + p1.w * A2[1];
+            if (c + 1 < LEN) w[c + 1] += p0.z * A1[0] + p0.w * A2[0] + p1.z * A1[1] + p1.w * A2[1];
         }
     }
 }
 
-// Contraction phase of step k: this CTA's slots, then its slab sums -> partial dots written into both
-// CTAs' part[rank] (and force moments added to A).  Ends before the cluster barrier X.
-template <int NC, int P>
-__device__ __forceinline__ void cluster_contract(const RecursionArgs<float> &args, const CSmem &S, float *part_remote,
-                                                 const CThread<NC, P> &th, const float (&vz)[NC], int k,
-                                                 bool need_dots, int nact, int nfrc, int amax, int fmax)
+// Warp part of the contraction phase of step k for z half H: projector dots (need_dots) and force
+// moments of the warp's (slab, half) into its slots.
+template <int NC, int P, int H>
+__device__ __forceinline__ void cluster_dots(const RecursionArgs<float> &args, const CSmem &S, const CThread<NC, P> &th,
+                                             const float (&vz)[CGeo<NC, P>::ZL], bool need_dots, int amax, int fmax)
 {
     using G = CGeo<NC, P>;
-    constexpr int NZ = G::NZ, NB0 = G::NB0, kHalf = G::HALF;
+    constexpr int NZP = G::NZP, NB0 = G::NB0, LEN = ZHalf<NC, P, H>::LEN;
     const int W = (amax + 31) / 32;
-    const int bl = th.w, a = th.a, lane = th.lane;
+    const int bl = th.bl, a = th.a, lane = th.lane;
     const bool live = th.live;
-    const int NTH = blockDim.x;
-    if (th.slab && (need_dots || args.want_force)) {
-        for (int wd = 0; wd < W; wd++) {
-            const unsigned all = S.ymask[bl * W + wd];
-            const unsigned fb = S.fbits[wd];
-            if (need_dots) {
-                const unsigned nf = all & ~fb, zl = S.zlo[wd], zh = S.zhi[wd];
-                cl_dots_pairs<NC, P, 0, kHalf + 1>(nf & zl, wd, S, vz, bl, a, live, lane, amax);
-                cl_dots_pairs<NC, P, kHalf, NC>(nf & zh, wd, S, vz, bl, a, live, lane, amax);
-                cl_dots_pairs<NC, P, 0, NC>(nf & ~(zl | zh), wd, S, vz, bl, a, live, lane, amax);
-            }
-            unsigned msk = args.want_force ? (all & fb) : 0u;
-            while (msk) {
-                const int t = 32 * wd + __ffs(msk) - 1;
-                msk &= msk - 1u;
-                const int fidx = S.rec[t].fidx;
-                const float4 *tz = S.tz + t * (NZ / 2);
-                const float4 *fz = S.fz + fidx * (NZ / 2);
-                float Ga = 0.f, Ha = 0.f, Gda = 0.f, Hda = 0.f, Gb = 0.f, Hb = 0.f, Gdb = 0.f, Hdb = 0.f;
+    if (!th.slab || !(need_dots || args.want_force)) return;
+    const float4 *tzh = S.tz + (size_t)H * amax * NZP;
+    const float4 *fzh = S.fz + (size_t)H * fmax * NZP;
+    float *slot = S.slot + ((size_t)bl * 2 + H) * amax * 4;
+    float *fslot = S.fslot + ((size_t)bl * 2 + H) * fmax * 12;
+    for (int wd = 0; wd < W; wd++) {
+        const unsigned all = S.ymask[bl * W + wd] & S.zmask[H * W + wd];
+        const unsigned fb = S.fbits[wd];
+        if (need_dots) cl_dots_pairs<NC, P, H>(all & ~fb, wd, S, vz, bl, a, live, lane, amax);
+        unsigned msk = args.want_force ? (all & fb) : 0u;
+        while (msk) {
+            const int t = 32 * wd + __ffs(msk) - 1;
+            msk &= msk - 1u;
+            const int fidx = S.rec[t].fidx;
+            const float4 *tz = tzh + t * NZP;
+            const float4 *fz = fzh + fidx * NZP;
+            float Ga = 0.f, Ha = 0.f, Gda = 0.f, Hda = 0.f, Gb = 0.f, Hb = 0.f, Gdb = 0.f, Hdb = 0.f;
 #pragma unroll
-                for (int c = 0; c < NC; c += 2) {
-                    const float4 z = tz[c >> 1], zd = fz[c >> 1];
-                    Ga += z.x * vz[c];
-                    Ha += z.y * vz[c];
-                    Gda += zd.x * vz[c];
-                    Hda += zd.y * vz[c];
-                    if (c + 1 < NC) {
-                        Gb += z.z * vz[c + 1];
-                        Hb += z.w * vz[c + 1];
-                        Gdb += zd.z * vz[c + 1];
-                        Hdb += zd.w * vz[c + 1];
-                    }
+            for (int c = 0; c < LEN; c += 2) {
+                const float4 z = tz[c >> 1], zd = fz[c >> 1];
+                Ga += z.x * vz[c];
+                Ha += z.y * vz[c];
+                Gda += zd.x * vz[c];
+                Hda += zd.y * vz[c];
+                if (c + 1 < LEN) {
+                    Gb += z.z * vz[c + 1];
+                    Hb += z.w * vz[c + 1];
+                    Gdb += zd.z * vz[c + 1];
+                    Hdb += zd.w * vz[c + 1];
                 }
-                const float Gs = Ga + Gb, Hs = Ha + Hb, Gd = Gda + Gdb, Hd = Hda + Hdb;
-                const float2 xv = live ? S.tx[t * NC + a] : make_float2(0.f, 0.f);
-                const float2 yv = S.ty[t * NB0 + bl];
-                float *sl = S.slot + ((size_t)bl * amax + t) * 4;
-                const float2 xd = live ? S.fx[fidx * NC + a] : make_float2(0.f, 0.f);
-                const float2 yd = S.fy[fidx * NB0 + bl];
-                const float v8[8] = {xv.x * Gs, xv.y * Gs, xv.x * Hs, xd.x * Gs, xv.x * Gd, xd.y * Gs, xv.y * Gd, xd.x * Hs};
-                const float red = reduce8(v8, lane);
-                const float v9 = wsum(xv.x * Hd);
-                const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                float *fs = S.fslot + ((size_t)bl * fmax + fidx) * 12;
-                if ((lane & 3) == 0) {
-                    switch (idx) {
-                    case 0: if (need_dots) { sl[0] = yv.x * red; sl[2] = yv.y * red; }
-                            fs[1] = yd.x * red; fs[7] = yd.y * red; break;
-                    case 1: if (need_dots) sl[1] = yv.x * red;
-                            fs[4] = yd.x * red; break;
-                    case 2: if (need_dots) sl[3] = yv.x * red;
-                            fs[10] = yd.x * red; break;
-                    case 3: fs[0] = yv.x * red; fs[6] = yv.y * red; break;
-                    case 4: fs[2] = yv.x * red; fs[8] = yv.y * red; break;
-                    case 5: fs[3] = yv.x * red; break;
-                    case 6: fs[5] = yv.x * red; break;
-                    default: fs[9] = yv.x * red; break;
-                    }
-                }
-                if (lane == 0) fs[11] = yv.x * v9;
             }
+            const float Gs = Ga + Gb, Hs = Ha + Hb, Gd = Gda + Gdb, Hd = Hda + Hdb;
+            const float2 xv = live ? S.tx[t * NC + a] : make_float2(0.f, 0.f);
+            const float2 yv = S.ty[t * NB0 + bl];
+            float *sl = slot + t * 4;
+            const float2 xd = live ? S.fx[fidx * NC + a] : make_float2(0.f, 0.f);
+            const float2 yd = S.fy[fidx * NB0 + bl];
+            const float v8[8] = {xv.x * Gs, xv.y * Gs, xv.x * Hs, xd.x * Gs, xv.x * Gd, xd.y * Gs, xv.y * Gd, xd.x * Hs};
+            const float red = reduce8(v8, lane);
+            const float v9 = wsum(xv.x * Hd);
+            const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+            float *fs = fslot + fidx * 12;
+            if ((lane & 3) == 0) {
+                switch (idx) {
+                case 0: if (need_dots) { sl[0] = yv.x * red; sl[2] = yv.y * red; }
+                        fs[1] = yd.x * red; fs[7] = yd.y * red; break;
+                case 1: if (need_dots) sl[1] = yv.x * red;
+                        fs[4] = yd.x * red; break;
+                case 2: if (need_dots) sl[3] = yv.x * red;
+                        fs[10] = yd.x * red; break;
+                case 3: fs[0] = yv.x * red; fs[6] = yv.y * red; break;
+                case 4: fs[2] = yv.x * red; fs[8] = yv.y * red; break;
+                case 5: fs[3] = yv.x * red; break;
+                case 6: fs[5] = yv.x * red; break;
+                default: fs[9] = yv.x * red; break;
+                }
+            }
+            if (lane == 0) fs[11] = yv.x * v9;
         }
     }
-    __syncthreads();
-    // fixed-order sums over this CTA's slabs
+}
+
+// CTA part of the contraction phase: fixed-order sums of this CTA's (slab, half) slots -> partial dots
+// written into both CTAs' part[rank], and force moments added to A.  Ends before the cluster barrier X.
+template <int NC, int P>
+__device__ __forceinline__ void cluster_slot_sums(const RecursionArgs<float> &args, const CSmem &S, float *part_remote,
+                                                  int rank, int k, bool need_dots, int nact, int nfrc, int amax,
+                                                  int fmax)
+{
+    constexpr int NB0 = CGeo<NC, P>::NB0;
+    const int W = (amax + 31) / 32;
+    const int NTH = blockDim.x;
     if (need_dots) {
-        float *mine = S.part + (size_t)th.rank * amax * 4;
-        float *theirs = part_remote + (size_t)th.rank * amax * 4;
+        float *mine = S.part + (size_t)rank * amax * 4;
+        float *theirs = part_remote + (size_t)rank * amax * 4;
         for (int it = threadIdx.x; it < nact * 4; it += NTH) {
             const int t = it >> 2, comp = it & 3;
+            const int wd = t >> 5;
+            const unsigned bit = 1u << (t & 31);
+            const bool in0 = S.zmask[wd] & bit, in1 = S.zmask[W + wd] & bit;
             float s = 0.f;
             for (int bb = 0; bb < NB0; bb++)
-                if ((S.ymask[bb * W + (t >> 5)] >> (t & 31)) & 1u) s += S.slot[((size_t)bb * amax + t) * 4 + comp];
+                if (S.ymask[bb * W + wd] & bit) {
+                    if (in0) s += S.slot[(((size_t)bb * 2 + 0) * amax + t) * 4 + comp];
+                    if (in1) s += S.slot[(((size_t)bb * 2 + 1) * amax + t) * 4 + comp];
+                }
             mine[it] = s;
             theirs[it] = s;
         }
@@ -488,11 +520,15 @@ __device__ __forceinline__ void cluster_contract(const RecursionArgs<float> &arg
         for (int it = threadIdx.x; it < nfrc * nf; it += NTH) {
             const int fi = it / nf, i = it % nf;
             const int t = S.ftl[fi];
+            const int wd = t >> 5;
+            const unsigned bit = 1u << (t & 31);
+            const bool in0 = S.zmask[wd] & bit, in1 = S.zmask[W + wd] & bit;
             double s = 0.0;
             bool any = false;
             for (int bb = 0; bb < NB0; bb++)
-                if ((S.ymask[bb * W + (t >> 5)] >> (t & 31)) & 1u) {
-                    s += (double)S.fslot[((size_t)bb * fmax + fi) * 12 + i];
+                if (S.ymask[bb * W + wd] & bit) {
+                    if (in0) s += (double)S.fslot[(((size_t)bb * 2 + 0) * fmax + fi) * 12 + i];
+                    if (in1) s += (double)S.fslot[(((size_t)bb * 2 + 1) * fmax + fi) * 12 + i];
                     any = true;
                 }
             const int lm = i / 3, d = i % 3;
@@ -503,12 +539,95 @@ __device__ __forceinline__ void cluster_contract(const RecursionArgs<float> &arg
     }
 }
 
+// Local part of Hhat v_k for z half H: stencil and diagonal into w (z neighbours from registers within
+// the half, from the shared buffer across the split).
+template <int NC, int P, int H>
+__device__ __forceinline__ void cluster_local(const RecursionArgs<float> &args, const CSmem &S, const CThread<NC, P> &th,
+                                              const float (&vz)[CGeo<NC, P>::ZL], float (&w)[CGeo<NC, P>::ZL],
+                                              const float *drow, int plane_p)
+{
+    using G = CGeo<NC, P>;
+    constexpr int NR = G::NR, ZL = G::ZL, Z0 = ZHalf<NC, P, H>::Z0, LEN = ZHalf<NC, P, H>::LEN;
+    const float *col = S.U + (size_t)th.row * NC + th.a;   // (z = 0, this row, this x)
+#pragma unroll
+    for (int c = 0; c < ZL; c++) {
+        const int zg = Z0 + c;
+        const float x = vz[c];
+        float t = 0.f;
+#pragma unroll
+        for (int j = 1; j <= P; j++) {
+            float zp = 0.f, zm = 0.f;
+            if (c + j < LEN) zp = vz[c + j];
+            else if (zg + j < NC && c < LEN) zp = th.live ? col[(size_t)(zg + j) * NR * NC] : 0.f;
+            if (c - j >= 0) zm = vz[c - j];
+            else if (zg - j >= 0 && c < LEN) zm = th.live ? col[(size_t)(zg - j) * NR * NC] : 0.f;
+            t += args.w[2][j - 1] * (zp + zm);
+        }
+#pragma unroll
+        for (int j = 1; j <= P; j++) t = xpair(t, x, j, args.w[0][j - 1]);
+        if (th.live && c < LEN) {
+            const float *row = col + (size_t)zg * NR * NC;
+#pragma unroll
+            for (int j = 1; j <= P; j++) {
+                const float yp = (th.yvalid >> (2 * j - 2)) & 1u ? row[j * NC] : 0.f;
+                const float ym = (th.yvalid >> (2 * j - 1)) & 1u ? row[-j * NC] : 0.f;
+                t += args.w[1][j - 1] * (yp + ym);
+            }
+            w[c] = t + drow[zg * plane_p] * x;
+        } else {
+            w[c] = 0.f;
+        }
+        // keep the loads of one z point from being hoisted into the next ones (register pressure)
+        asm volatile("" ::: "memory");
+    }
+}
+
+// KB term of Hhat v_k for z half H, added into w.
+template <int NC, int P, int H>
+__device__ __forceinline__ void cluster_kb(const CSmem &S, const CThread<NC, P> &th, float (&w)[CGeo<NC, P>::ZL],
+                                           float kap0, float kap1, int amax)
+{
+    const int W = (amax + 31) / 32;
+    if (!th.slab) return;
+    for (int wd = 0; wd < W; wd++) {
+        const unsigned all = S.ymask[th.bl * W + wd] & S.zmask[H * W + wd];
+        cl_update_pairs<NC, P, H>(all, wd, S, w, th.bl, th.a, th.live, kap0, kap1, amax);
+    }
+}
+
+// v_{k+1} = ca Hhat v_k - cb v_{k-1} for z half H: v_{k-1} from the CTA's scratch, v_k from the own
+// rows (it moves into the scratch), v_{k+1} into the own rows, the partner's halo rows and vz.
+// own, rem and pv point at z = 0 of this thread's own row, its row in the partner's buffer (when
+// prow >= 0) and its scratch pencil; the z planes are reached by constant offsets.
+template <int NC, int P, int H>
+__device__ __forceinline__ void cluster_finish(const CThread<NC, P> &th, const float (&w)[CGeo<NC, P>::ZL],
+                                               float (&vz)[CGeo<NC, P>::ZL], float *own, float *rem, float *pv,
+                                               float ca, float cb, bool first)
+{
+    using G = CGeo<NC, P>;
+    constexpr int NR = G::NR, NB0 = G::NB0, ZL = G::ZL, Z0 = ZHalf<NC, P, H>::Z0, LEN = ZHalf<NC, P, H>::LEN;
+#pragma unroll
+    for (int c = 0; c < ZL; c++) {
+        if (th.live && c < LEN) {
+            const int zg = Z0 + c;
+            const float vkm1 = first ? 0.f : pv[zg * NB0 * 32];
+            const float nv = ca * w[c] - cb * vkm1;
+            pv[zg * NB0 * 32] = own[zg * NR * NC];
+            own[zg * NR * NC] = nv;
+            vz[c] = nv;
+            if (th.prow >= 0) rem[zg * NR * NC] = nv;
+        } else {
+            vz[c] = 0.f;
+        }
+    }
+}
+
 template <int NC, int P>
 __global__ void __launch_bounds__(CGeo<NC, P>::NW * 32, 1) cluster_kernel(const RecursionArgs<float> args, int amax,
                                                                          int fmax, int *err)
 {
     using G = CGeo<NC, P>;
-    constexpr int NZ = G::NZ, NR = G::NR, kHalf = G::HALF;
+    constexpr int NZP = G::NZP, NR = G::NR, ZL = G::ZL;
     static_assert(P <= 6, "x shuffles assume a half-width of at most 6");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -518,105 +637,67 @@ __global__ void __launch_bounds__(CGeo<NC, P>::NW * 32, 1) cluster_kernel(const 
     cluster_layout<NC, P>(smem_raw, amax, fmax, &S);
     float *U_remote = cluster.map_shared_rank(S.U, partner);
     float *part_remote = cluster.map_shared_rank(S.part, partner);
+    float *vprev = args.scratch + (size_t)blockIdx.x * G::SCR;
     const CThread<NC, P> th(rank);
-    const int m = (NC - 1) / 2;
     const long long N_d = args.N_d;
     const size_t plane_p = (size_t)args.pn[0] * args.pn[1];
     const long long ncl = gridDim.x / 2;
     const long long cid = blockIdx.x / 2;
     const float kap0 = args.kappa[0], kap1 = args.kappa[1];
-    const int W = (amax + 31) / 32;
+    float *own = S.U + (size_t)th.row * NC + th.a;
+    float *rem = U_remote + (size_t)(th.prow >= 0 ? th.prow : 0) * NC + th.a;
+    float *pv = vprev + (size_t)th.bl * 32 + th.lane;
+    // the centre point (m, m, m) lies in z half mh, pencil index mc
+    constexpr int m = (NC - 1) / 2;
+    constexpr int mh = m < G::ZS ? 0 : 1, mc = m - mh * G::ZS;
 
-    for (int i = threadIdx.x; i < NZ / 2; i += blockDim.x) S.zero[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < NZP; i += blockDim.x) S.zero[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     cluster.sync();   // both CTAs are running before any write into the partner's shared memory
 
     for (long long q = args.q0 + cid; q < args.q1; q += ncl) {
         int qa[3], nfrc = 0;
         const int nact = cluster_setup<NC, P>(args, S, q, amax, fmax, err, qa, &nfrc, rank);
         if (nact < 0) continue;   // both CTAs see the same count
-        // ---- v_0 = e_q (registers, own rows, the partner's halo rows), v_{-1} = 0 ----
-        float vz[NC], vp[NC];
+        // ---- v_0 = e_q (registers, own rows, the partner's halo rows) ----
+        float vz[ZL];
+        const int z0 = th.zh * G::ZS, len = th.zh ? NC - G::ZS : G::ZS;
 #pragma unroll
-        for (int c = 0; c < NC; c++) {
-            vz[c] = (th.centre_xy && c == m) ? 1.0f : 0.0f;
-            vp[c] = 0.f;
-            if (th.live) {
-                S.U[((size_t)c * NR + th.row) * NC + th.a] = vz[c];
-                if (th.prow >= 0) U_remote[((size_t)c * NR + th.prow) * NC + th.a] = vz[c];
+        for (int c = 0; c < ZL; c++) {
+            vz[c] = (th.centre_xy && th.zh == mh && c == mc) ? 1.0f : 0.0f;
+            if (th.live && c < len) {
+                S.U[((size_t)(z0 + c) * NR + th.row) * NC + th.a] = vz[c];
+                if (th.prow >= 0) U_remote[((size_t)(z0 + c) * NR + th.prow) * NC + th.a] = vz[c];
             }
         }
-        if (th.centre_xy) args.mu[q] = 1.0f;
+        if (th.centre_xy && th.zh == mh) args.mu[q] = 1.0f;
         const float *drow = args.dpad + (size_t)qa[2] * plane_p + (size_t)(qa[1] + (th.slab ? th.b : 0)) * args.pn[0] +
                             qa[0] + (th.live ? th.a : 0);
 
         for (int k = 0; k <= args.K; k++) {
             const bool need_dots = k < args.K;
-            cluster_contract<NC, P>(args, S, part_remote, th, vz, k, need_dots, nact, nfrc, amax, fmax);
-            cluster.sync();   // X: partial dots of both CTAs, and the halo rows of v_k, are visible
+            if (th.zh == 0) cluster_dots<NC, P, 0>(args, S, th, vz, need_dots, amax, fmax);
+            else cluster_dots<NC, P, 1>(args, S, th, vz, need_dots, amax, fmax);
+            __syncthreads();
+            cluster_slot_sums<NC, P>(args, S, part_remote, rank, k, need_dots, nact, nfrc, amax, fmax);
+            cluster.sync();   // X: partial dots of both CTAs, the halo rows and the other z half are visible
             if (!need_dots) break;
             for (int it = threadIdx.x; it < nact * 4; it += blockDim.x) S.sd[it] = S.part[it] + S.part[amax * 4 + it];
             __syncthreads();
             const float ca = k == 0 ? 1.f : 2.f, cb = k == 0 ? 0.f : 1.f;
-            // ---- local part of Hhat v_k: stencil and diagonal ----
-            float w[NC];
-#pragma unroll
-            for (int c = 0; c < NC; c++) {
-                const float x = vz[c];
-                float t = 0.f;
-#pragma unroll
-                for (int j = 1; j <= P; j++) {
-                    const float zp = (c + j < NC) ? vz[c + j] : 0.f;
-                    const float zm = (c - j >= 0) ? vz[c - j] : 0.f;
-                    t += args.w[2][j - 1] * (zp + zm);
-                }
-#pragma unroll
-                for (int j = 1; j <= P; j++) t = xpair(t, x, j, args.w[0][j - 1]);
-                if (th.live) {
-                    const float *row = S.U + ((size_t)c * NR + th.row) * NC + th.a;
-#pragma unroll
-                    for (int j = 1; j <= P; j++) {
-                        const float yp = (th.yvalid >> (2 * j - 2)) & 1u ? row[j * NC] : 0.f;
-                        const float ym = (th.yvalid >> (2 * j - 1)) & 1u ? row[-j * NC] : 0.f;
-                        t += args.w[1][j - 1] * (yp + ym);
-                    }
-                    w[c] = t + drow[(size_t)c * plane_p] * x;
-                } else {
-                    w[c] = 0.f;
-                }
-            }
+            float w[ZL];
+            if (th.zh == 0) cluster_local<NC, P, 0>(args, S, th, vz, w, drow, (int)plane_p);
+            else cluster_local<NC, P, 1>(args, S, th, vz, w, drow, (int)plane_p);
             // Y (arrive): this CTA's reads of v_k's buffer are done
             __syncwarp();
             auto y_token = cluster.barrier_arrive();
-            // ---- KB term ----
-            if (th.slab) {
-                for (int wd = 0; wd < W; wd++) {
-                    const unsigned all = S.ymask[th.w * W + wd], zl = S.zlo[wd], zh = S.zhi[wd];
-                    cl_update_pairs<NC, P, 0, kHalf + 1>(all & zl, wd, S, w, th.w, th.a, th.live, kap0, kap1);
-                    cl_update_pairs<NC, P, kHalf, NC>(all & zh, wd, S, w, th.w, th.a, th.live, kap0, kap1);
-                    cl_update_pairs<NC, P, 0, NC>(all & ~(zl | zh), wd, S, w, th.w, th.a, th.live, kap0, kap1);
-                }
-            }
+            if (th.zh == 0) cluster_kb<NC, P, 0>(S, th, w, kap0, kap1, amax);
+            else cluster_kb<NC, P, 1>(S, th, w, kap0, kap1, amax);
             // Y (wait): both CTAs are done reading v_k's buffers
             __syncwarp();
             cluster.barrier_wait(std::move(y_token));
-            // ---- v_{k+1} = ca Hhat v_k - cb v_{k-1}; v_k becomes v_{k-1} ----
-#pragma unroll
-            for (int c = 0; c < NC; c++) {
-                if (th.live) {
-                    // v_k comes back from the own row it still occupies, so its registers are free
-                    // during the KB update
-                    float *own = S.U + ((size_t)c * NR + th.row) * NC + th.a;
-                    const float nv = ca * w[c] - cb * vp[c];
-                    vp[c] = *own;
-                    vz[c] = nv;
-                    *own = nv;
-                    if (th.prow >= 0) U_remote[((size_t)c * NR + th.prow) * NC + th.a] = nv;
-                } else {
-                    vp[c] = 0.f;
-                    vz[c] = 0.f;
-                }
-            }
-            if (th.centre_xy) args.mu[(size_t)(k + 1) * N_d + q] = vz[m];
+            if (th.zh == 0) cluster_finish<NC, P, 0>(th, w, vz, own, rem, pv, ca, cb, k == 0);
+            else cluster_finish<NC, P, 1>(th, w, vz, own, rem, pv, ca, cb, k == 0);
+            if (th.centre_xy && th.zh == mh) args.mu[(size_t)(k + 1) * N_d + q] = vz[mc];
         }
     }
     cluster.sync();   // no CTA leaves while its partner may still write into its shared memory
@@ -671,6 +752,11 @@ cudaError_t cluster_launch(const RecursionArgs<float> &args, int amax, int fmax,
 }
 
 }  // namespace
+
+long long cluster_scratch_floats(int nc)
+{
+    return nc == 29 ? (long long)CGeo<29, 6>::SCR : 0;
+}
 
 bool cluster_supported(const int nc[3], int fd_half)
 {

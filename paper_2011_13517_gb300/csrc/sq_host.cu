@@ -969,6 +969,10 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, long long q0,
                 maxc > 0) {
                 long long ncl = maxc;
                 if (ncl > q1 - q0) ncl = q1 - q0;
+                if ((s = ensure(&h->d_scratch, &h->scratch_cap,
+                                sizeof(float) * (size_t)cluster_scratch_floats(h->nc[0]) * 2 * ncl)))
+                    return s;
+                a.scratch = reinterpret_cast<T *>(h->d_scratch);
                 h->kernel_used = 2;
                 SQ_CUDA(cudaEventRecord(h->ev[0], stream));
                 SQ_COUNT(1);
@@ -1906,6 +1910,8 @@ struct sq_batch_s {
     std::vector<size_t> slab_smem;
     std::vector<int> slab_kind;               // 1: slab kernel (21^3, 25^3), 2: cluster kernel (29^3)
     std::vector<int> slab_ncl;                // clusters of a cluster launch
+    void *d_cscratch = nullptr;               // v_{k-1} scratch of the cluster launches
+    size_t cscratch_cap = 0;
 };
 
 extern "C" void sq_batch_destroy(sq_batch b)
@@ -1919,6 +1925,7 @@ extern "C" void sq_batch_destroy(sq_batch b)
     cudaFree(b->d_items);
     cudaFree(b->d_counter);
     cudaFree(b->d_scratch);
+    cudaFree(b->d_cscratch);
     delete b;
 }
 
@@ -2188,6 +2195,22 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
             b->chunk = 128;
         }
     }
+    // cells on the cluster kernel keep v_{k-1} in per-CTA scratch; their launches run one after
+    // another on the stream, so they share one buffer owned by the batch
+    if (sizeof(T) == 4) {
+        size_t need = 0;
+        for (int i = 0; i < nc; i++)
+            if (b->slab_kind[i] == 2)
+                need = std::max(need, sizeof(float) * (size_t)cluster_scratch_floats(b->cells[i]->nc[0]) * 2 *
+                                          (size_t)b->slab_ncl[i]);
+        if (need > 0) {
+            sq_status s = ensure(&b->d_cscratch, &b->cscratch_cap, need);
+            if (s) return s;
+            for (int i = 0; i < nc; i++)
+                if (b->slab_kind[i] == 2) args[i].scratch = reinterpret_cast<T *>(b->d_cscratch);
+        }
+    }
+
     // autotune once: kernel configuration x work-item size, timed on a prefix of the work queue
     if (b->config < 0) {
         SQ_CUDA(cudaStreamSynchronize(stream));

@@ -136,8 +136,10 @@ long long slab_vector_floats(int nc);
 
 // FP32 cluster kernel (cubic 29^3 cubes, 12th-order FD): a cluster of two CTAs per column, each
 // holding half of the cube's y-slabs.  Uses the slab kernel's capacity pre-pass (slab_counts).
-// cluster_prepare gives the shared memory per CTA and how many clusters fit on the GPU at once.
+// cluster_prepare gives the shared memory per CTA and how many clusters fit on the GPU at once; the
+// launch needs args.scratch with cluster_scratch_floats(nc) floats per CTA (2 per cluster).
 bool cluster_supported(const int nc[3], int fd_half);
+long long cluster_scratch_floats(int nc);
 cudaError_t cluster_prepare(int nc, int amax, int fmax, size_t *smem, int *max_clusters);
 cudaError_t launch_cluster(const RecursionArgs<float> &args, int amax, int fmax, int nclusters, size_t smem,
                            int *err, cudaStream_t stream);
