@@ -530,6 +530,7 @@ def main():
 
     # measured FMA ceilings of this GPU (outside the timed region)
     fma = {"fp32": sq.sq_fma_throughput(sq.SQ_FP32)[0], "fp64": sq.sq_fma_throughput(sq.SQ_FP64)[0]}
+    mma = {"tf32_m16n8k8": sq.sq_mma_throughput(0)[0], "bf16_m16n8k16": sq.sq_mma_throughput(1)[0]}
     flops_ball = algorithmic_flops_ball(main_cell)
     flops_box = algorithmic_flops(main_cell)
 
@@ -579,6 +580,7 @@ def main():
         "results": {"lambda_f": m["lam_f"], "U": m["U"], "S": m["S"]},
         "vs_oracle": m["vs_oracle"],
         "fma_peaks_tflops": fma,
+        "warp_mma_peaks_tflops": mma,
     }
     for p in precs[1:]:
         r = results[p]

@@ -311,6 +311,15 @@ long long sq_kernel_launches(void);
 sq_status sq_fma_throughput(int precision, double *tflops, double *ms, void *stream);
 
 /*
+ * sq_mma_throughput -- measured throughput of the warp-level tensor-core instruction (mma.sync) the
+ * per-warp contractions of the projector term could use instead of FMAs: kind 0 TF32 m16n8k8, kind 1
+ * BF16 m16n8k16, FP32 accumulation; 8 independent accumulator tiles per warp at full occupancy,
+ * timed with CUDA events on `stream` (about 100 ms).  Outputs: TFLOP/s and the timed launch's
+ * milliseconds (either may be NULL).  Errors: SQ_ERR_ARG, SQ_ERR_CUDA.
+ */
+sq_status sq_mma_throughput(int kind, double *tflops, double *ms, void *stream);
+
+/*
  * sq_moments_noalloc -- the Chebyshev moments mu_k^q (k = 0..K, every grid point) of the handle's
  * Hamiltonian, computed without any device allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot let the library allocate once their steady state has begun

@@ -31,7 +31,7 @@ EXPORTS = ["sq_build_hamiltonian", "sq_density", "sq_fermi_level", "sq_fermi_wei
            "sq_fermi_resolve",
            "sq_moments_range", "sq_moments_cols", "sq_observables", "sq_energy", "sq_nonlocal_force",
            "sq_get_spectral_bounds", "sq_get_moments", "sq_copy_moments", "sq_get_cube", "sq_get_timing",
-           "sq_kernel_launches", "sq_fma_throughput", "sq_moments_noalloc", "sq_batch_create", "sq_batch_density",
+           "sq_kernel_launches", "sq_fma_throughput", "sq_mma_throughput", "sq_moments_noalloc", "sq_batch_create", "sq_batch_density",
            "sq_batch_info", "sq_batch_destroy", "sq_density_vjp", "sq_kernel_name", "sq_destroy",
            "sq_status_string", "sq_last_error"]
 
@@ -77,6 +77,7 @@ def lib():
         L.sq_observables.argtypes = [vp, d, d, d, dp, dp, vp, vp]
         L.sq_moments_cols.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_longlong, vp, vp]
         L.sq_fma_throughput.argtypes = [ctypes.c_int, dp, dp, vp]
+        L.sq_mma_throughput.argtypes = [ctypes.c_int, dp, dp, vp]
         L.sq_energy.argtypes = [vp, dp, dp, dp, vp]
         L.sq_nonlocal_force.argtypes = [vp, vp, vp]
         L.sq_get_spectral_bounds.argtypes = [vp, dp, dp]
@@ -265,6 +266,13 @@ def sq_observables(h: Handle, lambda_f, kT, N_e, msum, A=None, d_rho=None, strea
                                 Ah.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if Ah is not None else None,
                                 _dev_ptr(d_rho, numel=n) if d_rho is not None else ctypes.c_void_p(None),
                                 _stream(stream)))
+
+
+def sq_mma_throughput(kind, stream=None):
+    """Measured warp-level MMA throughput (TFLOP/s, ms): kind 0 TF32 m16n8k8, 1 BF16 m16n8k16."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().sq_mma_throughput(int(kind), ctypes.byref(t), ctypes.byref(ms), _stream(stream)))
+    return t.value, ms.value
 
 
 def sq_fma_throughput(precision, stream=None):

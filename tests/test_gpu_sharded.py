@@ -99,3 +99,7 @@ def test_fma_probe_reports_the_pipes():
     t64, ms64 = sq.sq_fma_throughput(sq.SQ_FP64)
     print(f"FMA ceilings: FP32 {t32:.1f} TFLOP/s ({ms32:.1f} ms), FP64 {t64:.2f} TFLOP/s ({ms64:.1f} ms)")
     assert 10.0 < t32 < 200.0 and 0.1 < t64 < t32 and ms32 > 10 and ms64 > 10
+    tf, mtf = sq.sq_mma_throughput(0)
+    bf, mbf = sq.sq_mma_throughput(1)
+    print(f"warp-level MMA: TF32 m16n8k8 {tf:.1f} TFLOP/s ({mtf:.1f} ms), BF16 m16n8k16 {bf:.1f} TFLOP/s ({mbf:.1f} ms)")
+    assert tf > 1.0 and bf > 1.0 and mtf > 10 and mbf > 10
