@@ -232,7 +232,7 @@ def test_vjp_vacancy_pointwise_finite_differences(vacancy_vjp):
         gz = (pz + np.arange(-m[2], m[2] + 1)) % n[2]
         cols = (gx[None, None, :] + n[0] * (gy[None, :, None] + n[1] * gz[:, None, None])).reshape(-1)
         dcols = torch.from_numpy(cols.astype(np.int64)).cuda()
-        L = []
+        parts = []
         for sgn in (1.0, -1.0):
             v = veff.clone()
             v[int(p)] += sgn * eps
@@ -241,12 +241,17 @@ def test_vjp_vacancy_pointwise_finite_differences(vacancy_vjp):
             h.close()
             mu = out.view(K + 1, cols.size).cpu().numpy()
             dmu = mu - mu0[:, cols]
-            M = M0 + dmu.sum(axis=1)
-            R = R0 + dmu @ rho_bar[cols]
-            lam = sq.sq_fermi_level(M, K, omega, tau, lo, hi, c.kT, c.N_e)
+            dM = dmu.sum(axis=1)
+            dR = dmu @ rho_bar[cols]
+            lam = sq.sq_fermi_level(M0 + dM, K, omega, tau, lo, hi, c.kT, c.N_e)
             cw, dw, _ = sq.sq_fermi_weights(lam, K, omega, tau, c.kT)
-            L.append(2.0 / dV * float(cw @ R) + U_bar * 2.0 * float(dw @ M))
-        fd = (L[0] - L[1]) / (2 * eps)
+            parts.append((cw, dw, dM, dR))
+        # L = 2/dV c.(R0 + dR) + 2 U_bar d.(M0 + dM); the difference of the two sides is formed term by
+        # term, so the large common parts c.R0 and d.M0 (about 1e3) do not cancel in FP64 rounding
+        (cp, dp, dMp, dRp), (cm, dm, dMm, dRm) = parts
+        dL = (2.0 / dV * (float((cp - cm) @ R0) + float(cp @ dRp) - float(cm @ dRm))
+              + U_bar * 2.0 * (float((dp - dm) @ M0) + float(dp @ dMp) - float(dm @ dMm)))
+        fd = dL / (2 * eps)
         err = abs(fd - v64[p])
         worst = max(worst, err / scale)
         assert err < 1e-7 * scale + 1e-6 * abs(v64[p]), (int(p), fd, v64[p])
