@@ -367,6 +367,61 @@ def run_adjoint(args, sq, torch, world, rank, barrier, dist):
                           "config": dict(workload_config(c), checkpoint_k=kc)}), flush=True)
 
 
+def run_gauss(args, sq, torch, world, rank, barrier, dist):
+    """Gauss (Lanczos) spectral quadrature for rho, U and S (SQ_GAUSS) on the vacancy cell at its K:
+    per column K Lanczos steps, the Jacobi matrix's Gauss rule, the Fermi level over all nodes and the
+    observables, timed like the Chebyshev step (inputs resident, L2 flushed between steps)."""
+    precision = sq.SQ_FP64 if args.precision == "fp64" else sq.SQ_FP32
+    c = cells.vacancy_cell()
+    if args.profile:   # small case for ncu
+        c.K = 8
+    d_veff = torch.from_numpy(np.ascontiguousarray(c.veff.reshape(-1))).cuda()
+    rho = torch.empty(c.N_d, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    h = sq.build_for_cell(c, d_veff=d_veff)
+
+    def step():
+        return sq.sq_density(h, c.K, c.kT, c.N_e, precision, sq.SQ_GAUSS, rho)
+
+    if args.profile:
+        step()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "gauss", "K": c.K, "kernel": sq.sq_kernel_name(h)}), flush=True)
+        h.close()
+        return
+    for _ in range(args.warmup):
+        step()
+    times, lam = [], None
+    launches0 = sq.sq_kernel_launches()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lam = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    launches = (sq.sq_kernel_launches() - launches0) / max(1, args.steps)
+    U, S, _ = sq.sq_energy(h)
+    kname = sq.sq_kernel_name(h)
+    tim = sq.sq_get_timing(h)
+    h.close()
+    ms = statistics.mean(times)
+    if rank == 0:
+        print(json.dumps({"metric": "SQ density grid-points/sec, Gauss (Lanczos) quadrature", "unit": UNIT,
+                          "value": world * c.N_d / (ms * 1e-3), "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f32" if precision else "f64", "data": "synthetic",
+                          "config": dict(workload_config(c), quadrature="Gauss (Lanczos), SQ_GAUSS",
+                                         l2="flushed between steps (256 MiB write)"),
+                          "kernel": kname, "timing_ms": tim, "gpu_launches": launches,
+                          "results": {"lambda_f": lam, "U": U, "S": S}, "clocks": clk.summary()}), flush=True)
+
+
 def golden_errors(cell, lam, U, S, rho, force):
     """Errors of one result against the FP64 oracle's golden values of the same cell (written by
     tests/golden/make_golden.py): the rho error stated beside each throughput number."""
@@ -400,10 +455,14 @@ def main():
     ap.add_argument("--no-vacancy", action="store_true", help="skip the extra vacancy-cell line")
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed steps of the secondary FP64 measurement (0: same as --steps)")
-    ap.add_argument("--workload", choices=["precision", "vacancy", "batch", "adjoint"], default="precision",
+    ap.add_argument("--workload", choices=["precision", "vacancy", "batch", "adjoint", "gauss"], default="precision",
                     help="precision: the headline line (286-atom cell, 29^3 cubes, K=80); vacancy: the 95-atom "
                          "cell alone; batch: 32 defect cells in one graph-captured batch; adjoint: the "
-                         "reverse-mode derivative of the vacancy cell")
+                         "reverse-mode derivative of the vacancy cell; gauss: Gauss (Lanczos) quadrature on "
+                         "the vacancy cell")
+    ap.add_argument("--kb", choices=["mma", "fma"], default="mma",
+                    help="projector term of the FP32 cluster kernel (29^3 cubes): tensor cores (3xTF32 warp MMAs) "
+                         "or CUDA-core FMAs (SQ_KB_FMA)")
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu, no timing loop: one sq_density of the same cell with K=8 "
                          "(batch: the first four cells, K=8; adjoint: K=8, checkpoint every 4 steps)")
@@ -435,8 +494,12 @@ def main():
     if args.workload == "adjoint":
         run_adjoint(args, sq, torch, world, rank, barrier, dist)
         return
+    if args.workload == "gauss":
+        run_gauss(args, sq, torch, world, rank, barrier, dist)
+        return
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    KB_FLAGS = sq.SQ_KB_FMA if args.kb == "fma" else 0
 
     class Workload:
         def __init__(self, cell):
@@ -448,7 +511,8 @@ def main():
         def step(self, precision, K=None):
             c = self.cell
             h = sq.build_for_cell(c, d_veff=self.d_veff)
-            lam = sq.sq_density(h, c.K if K is None else K, c.kT, c.N_e, precision, sq.SQ_WANT_FORCE, self.rho)
+            lam = sq.sq_density(h, c.K if K is None else K, c.kT, c.N_e, precision, sq.SQ_WANT_FORCE | KB_FLAGS,
+                                self.rho)
             U, S, F = sq.sq_energy(h)
             sq.sq_nonlocal_force(h, self.force)
             timing = sq.sq_get_timing(h)
@@ -505,7 +569,7 @@ def main():
                 t0 = time.perf_counter()
                 dv.copy_(host_veff, non_blocking=True)
                 h = sq.build_for_cell(c, d_veff=dv)
-                sq.sq_density(h, c.K, c.kT, c.N_e, precision, sq.SQ_WANT_FORCE, self.rho)
+                sq.sq_density(h, c.K, c.kT, c.N_e, precision, sq.SQ_WANT_FORCE | KB_FLAGS, self.rho)
                 sq.sq_energy(h)
                 sq.sq_nonlocal_force(h, self.force)
                 host_rho.copy_(self.rho, non_blocking=True)
@@ -548,7 +612,10 @@ def main():
                 "peak_source": f"measured: sq_fma_throughput({p}) on this GPU in this run",
                 "peak_unit_count": unit_peak, "frac_of_unit_count": ach / unit_peak,
                 "unit_count_source": ("152 SM x 128 FP32 lanes x 2 x 2.07 GHz" if p == "fp32"
-                                      else "nominal GB300 FP64 rate")}
+                                      else "nominal GB300 FP64 rate"),
+                "projector_term": ("tensor cores: 3xTF32 warp MMAs (m16n8k8), FP32 accumulation; the stencil "
+                                   "and the rest on the FP32 pipes" if r["kernel"].endswith(",mma>")
+                                   else "FMA pipes")}
 
     precs = ["fp32", "fp64"] if args.precision == "both" else [args.precision]
     results = {}
@@ -574,7 +641,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": m["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if main_p == "fp32" else "f64", "data": "synthetic",
         "config": dict(workload_config(main_cell), parallelism=f"replicas x{world}" if world > 1 else "single GPU",
-                       recursion_precision=main_p),
+                       recursion_precision=main_p, projector_path=args.kb),
         "roofline": m["roofline"], "clocks": m["clocks"], "gpu_launches": m["launches"],
         "e2e": {"value": world * e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
         "results": {"lambda_f": m["lam_f"], "U": m["U"], "S": m["S"]},

@@ -58,8 +58,13 @@ enum { SQ_FP64 = 0, SQ_FP32 = 1 };
  *   truncated operator from e_q, the Jacobi matrix's eigenvalues as nodes and squared first
  *   eigenvector components as weights, the Fermi level over all nodes (Eq. Ne), and rho^q, u^q, s^q
  *   (Eqs. rhoq, uq, sq).  K <= 256; not combinable with SQ_WANT_FORCE (the paper takes the force
- *   from the Clenshaw-Curtis path); sq_energy then reports the Gauss U and S. */
-enum { SQ_WANT_FORCE = 1, SQ_GAUSS = 2 };
+ *   from the Clenshaw-Curtis path); sq_energy then reports the Gauss U and S.
+ * SQ_KB_FMA: FP32 recursion on 29^3 cubes only (the two-CTA cluster kernel): take the projector term
+ *   (chi^T v and the rank update) on the CUDA cores instead of the tensor cores.  By default that
+ *   kernel runs both as warp-level TF32 MMAs with each operand split into two TF32 parts (three
+ *   products, FP32 accumulation), which keep the products to about 2^-21 relative; the flag gives the
+ *   plain FP32 FMA form of the same sums, for comparison.  No effect on other kernels. */
+enum { SQ_WANT_FORCE = 1, SQ_GAUSS = 2, SQ_KB_FMA = 4 };
 
 /* flags of sq_build_hamiltonian: the gradient of the projectors in the nonlocal force.
  * SQ_GRAD_ANALYTIC: the analytic gradient of chi.
@@ -137,7 +142,7 @@ sq_status sq_build_hamiltonian(const sq_grid *grid, const double *d_veff, const 
  *   kT          smearing k_B theta (Ha), > 0
  *   N_e         electron count, 0 < N_e < 2 N_d
  *   precision   SQ_FP64 or SQ_FP32 (recursion precision)
- *   flags       0 or SQ_WANT_FORCE
+ *   flags       0 or SQ_WANT_FORCE, optionally with SQ_KB_FMA
  *   d_rho       device [N_d] FP64 output, caller-owned
  *   lambda_f    host double output (Fermi level, Ha)
  * Errors: SQ_ERR_ARG, SQ_ERR_NO_BRACKET, SQ_ERR_NOT_FINITE, SQ_ERR_OOM, SQ_ERR_CUDA.
@@ -214,7 +219,7 @@ sq_status sq_fermi_resolve(sq_handle h, double kT, double N_e, double *d_rho, do
  *     sq_observables    -> rho of its columns; then sq_energy and sq_nonlocal_force as usual.
  *
  * sq_moments_range -- the recursion (Eq. Chebyshev) for the columns q in [q_begin, q_end) only.
- *   K, precision, flags   as sq_density (flags: 0 or SQ_WANT_FORCE)
+ *   K, precision, flags   as sq_density (flags: 0 or SQ_WANT_FORCE, optionally with SQ_KB_FMA)
  *   q_begin, q_end        0 <= q_begin < q_end <= N_d
  *   msum        host [K+1] output: M_k summed over the range's columns (FP64)
  *   A           host [K+1][natom][nproj][3] output of the range's force moments
@@ -384,7 +389,8 @@ sq_status sq_density_vjp(sq_handle h, const double *d_rho_bar, double U_bar, int
  * share the FD order and the device).  Allocates every buffer the graph will use.
  *   cells[ncells]   handles from sq_build_hamiltonian (owned by the caller; keep them alive)
  *   K, kT, N_e      host [ncells] per-cell polynomial order, smearing and electron count
- *   precision       SQ_FP64 or SQ_FP32;  flags: 0 or SQ_WANT_FORCE
+ *   precision       SQ_FP64 or SQ_FP32;  flags: 0 or SQ_WANT_FORCE, optionally with SQ_KB_FMA (as
+ *                   sq_density; a 29^3 cell whose atom lists exceed the tensor-core path then needs it)
  * Errors: SQ_ERR_ARG, SQ_ERR_UNSUPPORTED, SQ_ERR_OOM, SQ_ERR_CUDA.
  */
 typedef struct sq_batch_s *sq_batch;

@@ -43,6 +43,10 @@ namespace {
 
 using namespace slabdev;
 
+// Row stride (floats) of the x factor rows: 32 x positions (zero past the cube) and 4 of padding, so
+// the tensor-core fragment loads of one warp spread over the shared-memory banks.
+constexpr int FAS = 36;
+
 template <int NC, int P>
 struct CGeo {
     static constexpr int NB0 = (NC + 1) / 2;              // y-slabs of rank 0 (rank 1 owns NC - NB0)
@@ -51,9 +55,17 @@ struct CGeo {
     static constexpr int HB = NB0 - P;                    // slab held in row 0 of rank 1's buffer
     static constexpr int ZS = (NC + 1) / 2;               // z split: half 0 holds z < ZS, half 1 the rest
     static constexpr int ZL = ZS;                         // pencil registers per thread
-    static constexpr int NZP = (ZL + 1) / 2;              // float4 z-table entries per atom and half
+    static constexpr int NZP = 8;                         // float4 z-table entries per atom and half (16 z,
+                                                          // the tensor-core path's two n-tiles)
     static constexpr int SCR = NC * NB0 * 32;             // floats of v_{k-1} scratch per CTA
-    static_assert(NC <= 32 && NC - NB0 + P <= NR && 2 * ZS >= NC, "layout");
+    // z-plane stride of the shared vector buffer: at least NR rows plus a 32-wide read past the last row,
+    // and 4 mod 32, so the tensor-core fragment accesses (8 z planes x 4 x, or 8 x by 4 z pairs) fall
+    // in distinct banks
+    static constexpr int PS = (NR * NC + 32 - NC - 4 + 31) / 32 * 32 + 4;
+    // z planes of the buffer: the cube plus zero planes that the tensor-core path's whole 16-z tiles
+    // of the upper half reach
+    static constexpr int NZU = NC > ZS + 16 ? NC : ZS + 16;
+    static_assert(NC <= 32 && NC - NB0 + P <= NR && 2 * ZS >= NC && ZL <= 2 * NZP, "layout");
 };
 template <int NC, int P, int H>
 struct ZHalf {
@@ -62,17 +74,18 @@ struct ZHalf {
 };
 
 struct CSmem {
-    float *U;          // [NC z][NR rows][NC x]: own slabs of v_k plus the partner's P boundary slabs
-    float2 *tx;        // [amax][NC]   (g, hp) along x
-    float2 *ty;        // [amax][NB0]  (g, hp) along y, own slabs
-    float4 *tz;        // [2][amax][NZP] per z half: (g[z], hp[z], g[z+1], hp[z+1]) from the half's first z
+    float *U;          // [NZU z][PS]: plane z holds [NR rows][NC x], own slabs of v_k plus the partner's P
+                       // boundary slabs; zero outside them
+    float *fa;         // [2 amax][FAS] x factor rows: row 2t = g, row 2t+1 = hp of active atom t, zero past NC
+    float2 *ty;        // [amax+1][NB0]  (g, hp) along y, own slabs
+    float4 *tz;        // [2][amax+1][NZP] per z half: (g[z], hp[z], g[z+1], hp[z+1]) from the half's first z
     float2 *fx;        // [fmax][NC]   (g', hp') of force atoms
     float2 *fy;        // [fmax][NB0]
     float4 *fz;        // [2][fmax][NZP]
     float *slot;       // [NB0][2][amax][4] per (slab, z half)
     float *fslot;      // [NB0][2][fmax][12]
     float *part;       // [2][amax][4]: partial dots of rank 0 and rank 1 (each written by its rank)
-    float *sd;         // [amax][4]: total dots
+    float *sd;         // [amax+1][4]: total dots
     SlabRec *rec;      // [amax]
     double *chiq;      // [fmax][4]
     int *ftl;          // [fmax]
@@ -82,6 +95,12 @@ struct CSmem {
     float4 *zero;      // [NZP]
     int *scan;         // [40]
 };
+
+// x factors (g, hp) of active atom t at cube x position a (zeros for lanes past the cube)
+__device__ __forceinline__ float2 xfac(const CSmem &S, int t, int a, bool live)
+{
+    return live ? make_float2(S.fa[2 * t * FAS + a], S.fa[(2 * t + 1) * FAS + a]) : make_float2(0.f, 0.f);
+}
 
 __host__ __device__ inline size_t c_align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -97,17 +116,18 @@ __host__ __device__ inline size_t cluster_layout(unsigned char *base, int amax, 
         return base ? base + o : nullptr;
     };
     unsigned char *p;
-    p = take(sizeof(float) * (size_t)NC * G::NR * NC);         if (s) s->U = (float *)p;
-    p = take(sizeof(float2) * (size_t)amax * NC);              if (s) s->tx = (float2 *)p;
-    p = take(sizeof(float2) * (size_t)amax * G::NB0);          if (s) s->ty = (float2 *)p;
-    p = take(sizeof(float4) * (size_t)2 * amax * G::NZP);      if (s) s->tz = (float4 *)p;
+    // the atom tables have one more entry, index amax, which stays zero (padding of the tensor-core tiles)
+    p = take(sizeof(float) * (size_t)G::NZU * G::PS);          if (s) s->U = (float *)p;
+    p = take(sizeof(float) * (size_t)2 * (amax + 1) * FAS);    if (s) s->fa = (float *)p;
+    p = take(sizeof(float2) * (size_t)(amax + 1) * G::NB0);    if (s) s->ty = (float2 *)p;
+    p = take(sizeof(float4) * (size_t)2 * (amax + 1) * G::NZP); if (s) s->tz = (float4 *)p;
     p = take(sizeof(float2) * (size_t)fmax * NC);              if (s) s->fx = (float2 *)p;
     p = take(sizeof(float2) * (size_t)fmax * G::NB0);          if (s) s->fy = (float2 *)p;
     p = take(sizeof(float4) * (size_t)2 * fmax * G::NZP);      if (s) s->fz = (float4 *)p;
     p = take(sizeof(float) * (size_t)G::NB0 * 2 * amax * 4);   if (s) s->slot = (float *)p;
     p = take(sizeof(float) * (size_t)G::NB0 * 2 * fmax * 12);  if (s) s->fslot = (float *)p;
     p = take(sizeof(float) * (size_t)2 * amax * 4);            if (s) s->part = (float *)p;
-    p = take(sizeof(float) * (size_t)amax * 4);                if (s) s->sd = (float *)p;
+    p = take(sizeof(float) * (size_t)(amax + 1) * 4);          if (s) s->sd = (float *)p;
     p = take(sizeof(SlabRec) * (size_t)amax);                  if (s) s->rec = (SlabRec *)p;
     p = take(sizeof(double) * (size_t)fmax * 4);               if (s) s->chiq = (double *)p;
     p = take(sizeof(int) * (size_t)fmax);                      if (s) s->ftl = (int *)p;
@@ -224,10 +244,13 @@ __device__ int cluster_setup(const RecursionArgs<float> &args, const CSmem &S, l
         const float *f2 = args.fac + (size_t)J * args.fac_stride + args.fac_off[2] + wstart[2] + z;
         return make_float2(f2[f0 * args.n[2]], f2[(f0 + 2) * args.n[2]]);
     };
-    for (int it = threadIdx.x; it < nact * NC; it += NTH) {
-        const int o = it % NC, t = it / NC;
-        const float *f0 = args.fac + (size_t)S.rec[t].J * args.fac_stride + args.fac_off[0] + wstart[0] + o;
-        S.tx[it] = make_float2(f0[0], f0[2 * args.n[0]]);
+    for (int it = threadIdx.x; it < nact * 2 * FAS; it += NTH) {
+        const int o = it % FAS, row = it / FAS;
+        float v = 0.f;
+        if (o < NC)
+            v = args.fac[(size_t)S.rec[row >> 1].J * args.fac_stride + args.fac_off[0] + wstart[0] + o +
+                         (row & 1) * 2 * args.n[0]];
+        S.fa[it] = v;
     }
     for (int it = threadIdx.x; it < nact * NB0; it += NTH) {
         const int o = it % NB0, t = it / NB0;
@@ -244,7 +267,7 @@ __device__ int cluster_setup(const RecursionArgs<float> &args, const CSmem &S, l
         const int zend = h ? NC : ZS;
         const float2 u = z < zend ? zfac(S.rec[t].J, z, 0) : make_float2(0.f, 0.f);
         const float2 v = z + 1 < zend ? zfac(S.rec[t].J, z + 1, 0) : make_float2(0.f, 0.f);
-        S.tz[((size_t)h * amax + t) * NZP + i] = make_float4(u.x, u.y, v.x, v.y);
+        S.tz[((size_t)h * (amax + 1) + t) * NZP + i] = make_float4(u.x, u.y, v.x, v.y);
     }
     int nfrc = 0;
     if (args.want_force) {
@@ -335,7 +358,7 @@ __device__ __forceinline__ void cl_dots_pairs(unsigned msk, int wd, const CSmem 
                                               int bl, int a, bool live, int lane, int amax)
 {
     constexpr int NZP = CGeo<NC, P>::NZP, NB0 = CGeo<NC, P>::NB0, LEN = ZHalf<NC, P, H>::LEN;
-    const float4 *tzh = S.tz + (size_t)H * amax * NZP;
+    const float4 *tzh = S.tz + (size_t)H * (amax + 1) * NZP;
     float *slot = S.slot + ((size_t)bl * 2 + H) * amax * 4;
     while (msk) {
         const int t0 = 32 * wd + __ffs(msk) - 1;
@@ -362,8 +385,7 @@ __device__ __forceinline__ void cl_dots_pairs(unsigned msk, int wd, const CSmem 
             }
         }
         const float G0 = G0a + G0b, H0 = H0a + H0b, G1 = G1a + G1b, H1 = H1a + H1b;
-        const float2 x0 = live ? S.tx[t0 * NC + a] : make_float2(0.f, 0.f);
-        const float2 x1 = live ? S.tx[t1 * NC + a] : make_float2(0.f, 0.f);
+        const float2 x0 = xfac(S, t0, a, live), x1 = xfac(S, t1, a, live);
         const float v8[8] = {x0.x * G0, x0.y * G0, x0.x * H0, x0.x * G0, x1.x * G1, x1.y * G1, x1.x * H1, x1.x * G1};
         const float red = reduce8(v8, lane);
         const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
@@ -382,7 +404,7 @@ __device__ __forceinline__ void cl_update_pairs(unsigned msk, int wd, const CSme
                                                 int bl, int a, bool live, float kap0, float kap1, int amax)
 {
     constexpr int NZP = CGeo<NC, P>::NZP, NB0 = CGeo<NC, P>::NB0, LEN = ZHalf<NC, P, H>::LEN;
-    const float4 *tzh = S.tz + (size_t)H * amax * NZP;
+    const float4 *tzh = S.tz + (size_t)H * (amax + 1) * NZP;
     while (msk) {
         const int t0 = 32 * wd + __ffs(msk) - 1;
         msk &= msk - 1u;
@@ -395,7 +417,7 @@ __device__ __forceinline__ void cl_update_pairs(unsigned msk, int wd, const CSme
             const int t = i ? t1 : t0;
             const float4 s = *reinterpret_cast<const float4 *>(S.sd + 4 * t);
             const float2 yv = S.ty[t * NB0 + bl];
-            const float2 xv = live ? S.tx[t * NC + a] : make_float2(0.f, 0.f);
+            const float2 xv = xfac(S, t, a, live);
             const float Pv = kap0 * s.x * yv.x + kap1 * s.z * yv.y;
             const float Qv = kap1 * s.w * yv.x;
             const float Rv = kap1 * s.y * yv.x;
@@ -413,11 +435,232 @@ __device__ __forceinline__ void cl_update_pairs(unsigned msk, int wd, const CSme
     }
 }
 
+// ---- projector term on the tensor cores ----------------------------------------------------------
+//
+// Per warp (slab b, z half) the projector term is two small dense products over the separable
+// factors of the atoms L whose support meets the warp's slab and half (two rows per atom: its x
+// factors g and hp):
+//   dots    C[f][z] = sum_x FA[f][x] v(x, b, z)          (16-row tiles of f, k = x, n = z),
+//           then per atom the z factors and the y factor of slab b (CUDA cores);
+//   update  W[x][z] = sum_f FA[f][x] Q_b[f][z]           (m = x, k = f, n = z), with
+//           Q_b[2t][z] = (kappa_0 s_t g_y + kappa_1 py_t hp_y) g_z + kappa_1 pz_t g_y hp_z and
+//           Q_b[2t+1][z] = kappa_1 px_t g_y g_z from the dots (s, px, py, pz) of atom t.
+// Both run as m16n8k8 TF32 warp MMAs with FP32 accumulation, each operand split into a TF32 head and
+// a TF32 tail (x = hi + lo, |x - hi - lo| <= 2^-22 |x|) and the product taken as lo*hi + hi*lo +
+// hi*hi ("3xTF32"), so the products keep about FP32 accuracy.  Fragment layouts of m16n8k8 .tf32
+// (g = lane / 4, t = lane % 4): A a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4); B b0 (k t, n g),
+// b1 (k t+4, n g); C c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1).
+
+__device__ __forceinline__ unsigned to_tf32(float x)
+{
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo)
+{
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2])
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// d += (ah + al)(bh + bl) without the al bl term, small terms first
+__device__ __forceinline__ void mma3(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4],
+                                     const unsigned (&bh)[2], const unsigned (&bl)[2])
+{
+    mma_tf32(d, al, bh);
+    mma_tf32(d, ah, bl);
+    mma_tf32(d, ah, bh);
+}
+
+// Largest atom list of one warp that the tensor-core path takes (two registers of list entries); a
+// longer list sets error 3, and the host redoes the launch with the CUDA-core projector term.
+constexpr int kMmaMaxList = 64;
+
+// The warp's ordered list of atoms whose support meets slab bl and z half H: lane j holds entry j in
+// l0 and entry 32 + j in l1 (-1 past the end).  Returns the list length (the same in every lane).
+template <int H>
+__device__ __forceinline__ int warp_atom_list(const CSmem &S, int bl, int W, int lane, int &l0, int &l1)
+{
+    int n = 0;
+    l0 = -1;
+    l1 = -1;
+    for (int wd = 0; wd < W; wd++) {
+        const unsigned msk = S.ymask[bl * W + wd] & S.zmask[H * W + wd];
+        const int c = __popc(msk);
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const int r = lane + 32 * e - n;
+            if (r >= 0 && r < c) {
+                unsigned mm = msk;
+                for (int i = 0; i < r; i++) mm &= mm - 1u;
+                const int v = 32 * wd + __ffs(mm) - 1;
+                if (e == 0) l0 = v;
+                else l1 = v;
+            }
+        }
+        n += c;
+    }
+    return n;
+}
+
+// Projector dots of every atom in the warp's list (nL <= kMmaMaxList) into the warp's slots, from v_k
+// in the warp's own rows of U.
+template <int NC, int P, int H>
+__device__ __forceinline__ void cl_dots_mma(const CSmem &S, const CThread<NC, P> &th, int l0, int l1, int nL, int amax)
+{
+    using G = CGeo<NC, P>;
+    constexpr int NR = G::NR, NZP = G::NZP, NB0 = G::NB0, Z0 = ZHalf<NC, P, H>::Z0, LEN = ZHalf<NC, P, H>::LEN;
+    const int g = th.lane >> 2, t = th.lane & 3;
+    const float4 *tzh = S.tz + (size_t)H * (amax + 1) * NZP;
+    float *slot = S.slot + ((size_t)th.bl * 2 + H) * amax * 4;
+    const float *urow = S.U + (size_t)th.row * NC;   // (z 0, own row, x 0)
+    for (int mt = 0; 8 * mt < nL; mt++) {
+        const int src = mt < 4 ? l0 : l1;
+        const int iA = 8 * mt + (g >> 1), iB = iA + 4;
+        // entries past the list take the zero atom (index amax)
+        const bool okA = iA < nL, okB = iB < nL;
+        const int sA = __shfl_sync(0xffffffffu, src, iA & 31), sB = __shfl_sync(0xffffffffu, src, iB & 31);
+        const int tA = okA ? sA : amax, tB = okB ? sB : amax;
+        const float *rA = S.fa + (size_t)(2 * tA + (g & 1)) * FAS;
+        const float *rB = S.fa + (size_t)(2 * tB + (g & 1)) * FAS;
+        float acc[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+            for (int i = 0; i < 4; i++) acc[nt][i] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < 4; ks++) {
+            const int x0 = 8 * ks + t, x1 = x0 + 4;
+            unsigned ah[4], al[4];
+            split_tf32(rA[x0], ah[0], al[0]);
+            split_tf32(rB[x0], ah[1], al[1]);
+            split_tf32(rA[x1], ah[2], al[2]);
+            split_tf32(rB[x1], ah[3], al[3]);
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++) {
+                // v at x = 8 ks + t (+4), z = Z0 + 8 nt + g: past the cube in x the loads reach the next
+                // row and past the half in z the other half or the zero planes, all finite; their
+                // products meet zero x factors (FA) or zero z factors (tz) below
+                const float *col = urow + (size_t)(Z0 + 8 * nt + g) * CGeo<NC, P>::PS;
+                unsigned bh[2], bo[2];
+                split_tf32(col[x0], bh[0], bo[0]);
+                split_tf32(col[x1], bh[1], bo[1]);
+                mma3(acc[nt], ah, al, bh, bo);
+            }
+        }
+        // z factors of the lane's two rows (z = 8 nt + 2t and 8 nt + 2t + 1 of the half)
+        float sA1 = 0.f, sA2 = 0.f, sB1 = 0.f, sB2 = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++) {
+            const float4 pa = tzh[tA * NZP + 4 * nt + t], pb = tzh[tB * NZP + 4 * nt + t];
+            sA1 += pa.x * acc[nt][0] + pa.z * acc[nt][1];
+            sA2 += pa.y * acc[nt][0] + pa.w * acc[nt][1];
+            sB1 += pb.x * acc[nt][2] + pb.z * acc[nt][3];
+            sB2 += pb.y * acc[nt][2] + pb.w * acc[nt][3];
+        }
+        // sum over the four lanes of a row pair (they hold different z)
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            sA1 += __shfl_xor_sync(0xffffffffu, sA1, o);
+            sA2 += __shfl_xor_sync(0xffffffffu, sA2, o);
+            sB1 += __shfl_xor_sync(0xffffffffu, sB1, o);
+            sB2 += __shfl_xor_sync(0xffffffffu, sB2, o);
+        }
+        // row g: x factor g (g even) or hp (g odd) of atom A; row g + 8 likewise of atom B
+        if (t < 2 && (t == 0 ? okA : okB)) {
+            const int at = t == 0 ? tA : tB;
+            const float s1 = t == 0 ? sA1 : sB1, s2 = t == 0 ? sA2 : sB2;
+            const float2 yv = S.ty[at * NB0 + th.bl];
+            float *sl = slot + at * 4;
+            if ((g & 1) == 0) {
+                sl[0] = yv.x * s1;   // s
+                sl[2] = yv.y * s1;   // p_y
+                sl[3] = yv.x * s2;   // p_z
+            } else {
+                sl[1] = yv.x * s1;   // p_x
+            }
+        }
+    }
+}
+
+// Projector term of Hhat v_k over the warp's (slab, half) block on the tensor cores: acc[mt][nt]
+// holds W[x][z] for x = 16 mt + (g, g+8) and z = 8 nt + (2t, 2t+1) of the half.
+template <int NC, int P, int H>
+__device__ __forceinline__ void cl_kb_mma(const CSmem &S, const CThread<NC, P> &th, int l0, int l1, int nL,
+                                          float kap0, float kap1, int amax, float (&acc)[2][2][4])
+{
+    using G = CGeo<NC, P>;
+    constexpr int NZP = G::NZP, NB0 = G::NB0;
+    const int g = th.lane >> 2, t = th.lane & 3, fac = t & 1;
+    const float2 *tzh = reinterpret_cast<const float2 *>(S.tz + (size_t)H * (amax + 1) * NZP);
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+            for (int i = 0; i < 4; i++) acc[mt][nt][i] = 0.f;
+    for (int ks = 0; 4 * ks < nL; ks++) {
+        // rows 8 ks + j of FA / Q: atom 4 ks + j/2, factor j % 2; this lane holds j = t and t + 4
+        const int src = ks < 8 ? l0 : l1;
+        const int i0 = 4 * ks + (t >> 1), i1 = i0 + 2;
+        // entries past the list take the zero atom (index amax)
+        const int s0 = __shfl_sync(0xffffffffu, src, i0 & 31), s1 = __shfl_sync(0xffffffffu, src, i1 & 31);
+        const int t0 = i0 < nL ? s0 : amax, t1 = i1 < nL ? s1 : amax;
+        // Q rows of the two atoms: Q(z) = c1 g_z(z) + c2 hp_z(z)
+        float c1[2], c2[2];
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int at = r ? t1 : t0;
+            const float4 sv = *reinterpret_cast<const float4 *>(S.sd + 4 * at);
+            const float2 yv = S.ty[at * NB0 + th.bl];
+            if (fac == 0) {
+                c1[r] = kap0 * sv.x * yv.x + kap1 * sv.z * yv.y;
+                c2[r] = kap1 * sv.w * yv.x;
+            } else {
+                c1[r] = kap1 * sv.y * yv.x;
+                c2[r] = 0.f;
+            }
+        }
+        unsigned bh[2][2], bo[2][2];
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++) {
+            const int zl = 8 * nt + g;   // < 2 NZP: the half's z table covers it (zeros past the half)
+            const float2 p0 = tzh[t0 * 2 * NZP + zl], p1 = tzh[t1 * 2 * NZP + zl];
+            split_tf32(c1[0] * p0.x + c2[0] * p0.y, bh[nt][0], bo[nt][0]);
+            split_tf32(c1[1] * p1.x + c2[1] * p1.y, bh[nt][1], bo[nt][1]);
+        }
+        const float *r0 = S.fa + (size_t)(2 * t0 + fac) * FAS;
+        const float *r1 = S.fa + (size_t)(2 * t1 + fac) * FAS;
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++) {
+            const int x = 16 * mt + g;
+            unsigned ah[4], al[4];
+            split_tf32(r0[x], ah[0], al[0]);
+            split_tf32(r0[x + 8], ah[1], al[1]);
+            split_tf32(r1[x], ah[2], al[2]);
+            split_tf32(r1[x + 8], ah[3], al[3]);
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++) mma3(acc[mt][nt], ah, al, bh[nt], bo[nt]);
+        }
+    }
+}
+
 // Warp part of the contraction phase of step k for z half H: projector dots (need_dots) and force
-// moments of the warp's (slab, half) into its slots.
+// moments of the warp's (slab, half) into its slots.  With dots_fma false the dots of every atom come
+// from the tensor-core pass (cl_dots_mma) and this pass adds only the force moments.
 template <int NC, int P, int H>
 __device__ __forceinline__ void cluster_dots(const RecursionArgs<float> &args, const CSmem &S, const CThread<NC, P> &th,
-                                             const float (&vz)[CGeo<NC, P>::ZL], bool need_dots, int amax, int fmax)
+                                             const float (&vz)[CGeo<NC, P>::ZL], bool need_dots, bool dots_fma,
+                                             int amax, int fmax)
 {
     using G = CGeo<NC, P>;
     constexpr int NZP = G::NZP, NB0 = G::NB0, LEN = ZHalf<NC, P, H>::LEN;
@@ -425,14 +668,15 @@ __device__ __forceinline__ void cluster_dots(const RecursionArgs<float> &args, c
     const int bl = th.bl, a = th.a, lane = th.lane;
     const bool live = th.live;
     if (!th.slab || !(need_dots || args.want_force)) return;
-    const float4 *tzh = S.tz + (size_t)H * amax * NZP;
+    const float4 *tzh = S.tz + (size_t)H * (amax + 1) * NZP;
     const float4 *fzh = S.fz + (size_t)H * fmax * NZP;
     float *slot = S.slot + ((size_t)bl * 2 + H) * amax * 4;
     float *fslot = S.fslot + ((size_t)bl * 2 + H) * fmax * 12;
     for (int wd = 0; wd < W; wd++) {
         const unsigned all = S.ymask[bl * W + wd] & S.zmask[H * W + wd];
         const unsigned fb = S.fbits[wd];
-        if (need_dots) cl_dots_pairs<NC, P, H>(all & ~fb, wd, S, vz, bl, a, live, lane, amax);
+        const bool sl_on = need_dots && dots_fma;
+        if (sl_on) cl_dots_pairs<NC, P, H>(all & ~fb, wd, S, vz, bl, a, live, lane, amax);
         unsigned msk = args.want_force ? (all & fb) : 0u;
         while (msk) {
             const int t = 32 * wd + __ffs(msk) - 1;
@@ -456,7 +700,7 @@ __device__ __forceinline__ void cluster_dots(const RecursionArgs<float> &args, c
                 }
             }
             const float Gs = Ga + Gb, Hs = Ha + Hb, Gd = Gda + Gdb, Hd = Hda + Hdb;
-            const float2 xv = live ? S.tx[t * NC + a] : make_float2(0.f, 0.f);
+            const float2 xv = xfac(S, t, a, live);
             const float2 yv = S.ty[t * NB0 + bl];
             float *sl = slot + t * 4;
             const float2 xd = live ? S.fx[fidx * NC + a] : make_float2(0.f, 0.f);
@@ -468,11 +712,11 @@ __device__ __forceinline__ void cluster_dots(const RecursionArgs<float> &args, c
             float *fs = fslot + fidx * 12;
             if ((lane & 3) == 0) {
                 switch (idx) {
-                case 0: if (need_dots) { sl[0] = yv.x * red; sl[2] = yv.y * red; }
+                case 0: if (sl_on) { sl[0] = yv.x * red; sl[2] = yv.y * red; }
                         fs[1] = yd.x * red; fs[7] = yd.y * red; break;
-                case 1: if (need_dots) sl[1] = yv.x * red;
+                case 1: if (sl_on) sl[1] = yv.x * red;
                         fs[4] = yd.x * red; break;
-                case 2: if (need_dots) sl[3] = yv.x * red;
+                case 2: if (sl_on) sl[3] = yv.x * red;
                         fs[10] = yd.x * red; break;
                 case 3: fs[0] = yv.x * red; fs[6] = yv.y * red; break;
                 case 4: fs[2] = yv.x * red; fs[8] = yv.y * red; break;
@@ -558,15 +802,15 @@ __device__ __forceinline__ void cluster_local(const RecursionArgs<float> &args, 
         for (int j = 1; j <= P; j++) {
             float zp = 0.f, zm = 0.f;
             if (c + j < LEN) zp = vz[c + j];
-            else if (zg + j < NC && c < LEN) zp = th.live ? col[(size_t)(zg + j) * NR * NC] : 0.f;
+            else if (zg + j < NC && c < LEN) zp = th.live ? col[(size_t)(zg + j) * CGeo<NC, P>::PS] : 0.f;
             if (c - j >= 0) zm = vz[c - j];
-            else if (zg - j >= 0 && c < LEN) zm = th.live ? col[(size_t)(zg - j) * NR * NC] : 0.f;
+            else if (zg - j >= 0 && c < LEN) zm = th.live ? col[(size_t)(zg - j) * CGeo<NC, P>::PS] : 0.f;
             t += args.w[2][j - 1] * (zp + zm);
         }
 #pragma unroll
         for (int j = 1; j <= P; j++) t = xpair(t, x, j, args.w[0][j - 1]);
         if (th.live && c < LEN) {
-            const float *row = col + (size_t)zg * NR * NC;
+            const float *row = col + (size_t)zg * CGeo<NC, P>::PS;
 #pragma unroll
             for (int j = 1; j <= P; j++) {
                 const float yp = (th.yvalid >> (2 * j - 2)) & 1u ? row[j * NC] : 0.f;
@@ -612,17 +856,88 @@ __device__ __forceinline__ void cluster_finish(const CThread<NC, P> &th, const f
             const int zg = Z0 + c;
             const float vkm1 = first ? 0.f : pv[zg * NB0 * 32];
             const float nv = ca * w[c] - cb * vkm1;
-            pv[zg * NB0 * 32] = own[zg * NR * NC];
-            own[zg * NR * NC] = nv;
+            pv[zg * NB0 * 32] = own[zg * CGeo<NC, P>::PS];
+            own[zg * CGeo<NC, P>::PS] = nv;
             vz[c] = nv;
-            if (th.prow >= 0) rem[zg * NR * NC] = nv;
+            if (th.prow >= 0) rem[zg * CGeo<NC, P>::PS] = nv;
         } else {
             vz[c] = 0.f;
         }
     }
 }
 
+// Tensor-core path, first half of v_{k+1} = ca Hhat v_k - cb v_{k-1} for z half H: w (the local part)
+// becomes ca w - cb v_{k-1}, and v_k moves from the registers into the scratch in place of v_{k-1}.
+template <int NC, int P, int H>
+__device__ __forceinline__ void cluster_prefinish(const CThread<NC, P> &th, float (&w)[CGeo<NC, P>::ZL],
+                                                  const float (&vz)[CGeo<NC, P>::ZL], float *pv, float ca, float cb,
+                                                  bool first)
+{
+    using G = CGeo<NC, P>;
+    constexpr int NB0 = G::NB0, ZL = G::ZL, Z0 = ZHalf<NC, P, H>::Z0, LEN = ZHalf<NC, P, H>::LEN;
+#pragma unroll
+    for (int c = 0; c < ZL; c++) {
+        if (th.live && c < LEN) {
+            const int zg = Z0 + c;
+            const float vkm1 = first ? 0.f : pv[zg * NB0 * 32];
+            pv[zg * NB0 * 32] = vz[c];
+            w[c] = ca * w[c] - cb * vkm1;
+        }
+    }
+}
+
+// The warp's pencil of v_k from its own rows (zeros past the cube).
 template <int NC, int P>
+__device__ __forceinline__ void load_pencil(const CThread<NC, P> &th, const float *own, float (&v)[CGeo<NC, P>::ZL])
+{
+    using G = CGeo<NC, P>;
+    constexpr int NR = G::NR, ZL = G::ZL;
+    const int z0 = th.zh * G::ZS, len = th.zh ? NC - G::ZS : G::ZS;
+#pragma unroll
+    for (int c = 0; c < ZL; c++) v[c] = (th.live && c < len) ? own[(z0 + c) * CGeo<NC, P>::PS] : 0.f;
+}
+
+// Tensor-core path, second half (after the cluster barrier Y): the own rows receive w, then ca times
+// the projector term at the MMA fragment positions; the finished pencils go to the partner's halo rows
+// and, for the thread at the column's centre, mu_{k+1} to muk.
+template <int NC, int P, int H>
+__device__ __forceinline__ void cluster_finish_mma(const CSmem &S, const CThread<NC, P> &th,
+                                                   const float (&w)[CGeo<NC, P>::ZL], const float (&acc)[2][2][4],
+                                                   float *own, float *rem, float ca, float *muk, int mc)
+{
+    using G = CGeo<NC, P>;
+    constexpr int NR = G::NR, ZL = G::ZL, Z0 = ZHalf<NC, P, H>::Z0, LEN = ZHalf<NC, P, H>::LEN;
+#pragma unroll
+    for (int c = 0; c < ZL; c++)
+        if (th.live && c < LEN) own[(Z0 + c) * CGeo<NC, P>::PS] = w[c];
+    __syncwarp();
+    if (th.slab) {
+        const int g = th.lane >> 2, t = th.lane & 3;
+        float *base = S.U + (size_t)th.row * NC;
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int x = 16 * mt + g + ((i & 2) ? 8 : 0), zl = 8 * nt + 2 * t + (i & 1);
+                    if (x < NC && zl < LEN) base[(size_t)(Z0 + zl) * CGeo<NC, P>::PS + x] += ca * acc[mt][nt][i];
+                }
+    }
+    __syncwarp();
+    if (th.live && (th.prow >= 0 || muk)) {
+#pragma unroll
+        for (int c = 0; c < ZL; c++) {
+            if (c < LEN) {
+                const float nv = own[(Z0 + c) * CGeo<NC, P>::PS];
+                if (th.prow >= 0) rem[(Z0 + c) * CGeo<NC, P>::PS] = nv;
+                if (muk && c == mc) *muk = nv;
+            }
+        }
+    }
+}
+
+template <int NC, int P, bool MMA>
 __global__ void __launch_bounds__(CGeo<NC, P>::NW * 32, 1) cluster_kernel(const RecursionArgs<float> args, int amax,
                                                                          int fmax, int *err)
 {
@@ -652,64 +967,132 @@ __global__ void __launch_bounds__(CGeo<NC, P>::NW * 32, 1) cluster_kernel(const 
     constexpr int mh = m < G::ZS ? 0 : 1, mc = m - mh * G::ZS;
 
     for (int i = threadIdx.x; i < NZP; i += blockDim.x) S.zero[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // zero the vector buffer (rows and planes that no slab fills stay zero) and the zero atom's entries
+    for (int i = threadIdx.x; i < G::NZU * G::PS; i += blockDim.x) S.U[i] = 0.f;
+    for (int i = threadIdx.x; i < 2 * FAS; i += blockDim.x) S.fa[2 * amax * FAS + i] = 0.f;
+    for (int i = threadIdx.x; i < G::NB0; i += blockDim.x) S.ty[(size_t)amax * G::NB0 + i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < 2 * NZP; i += blockDim.x)
+        S.tz[((size_t)(i / NZP) * (amax + 1) + amax) * NZP + i % NZP] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < 4; i += blockDim.x) S.sd[4 * amax + i] = 0.f;
     cluster.sync();   // both CTAs are running before any write into the partner's shared memory
 
     for (long long q = args.q0 + cid; q < args.q1; q += ncl) {
         int qa[3], nfrc = 0;
         const int nact = cluster_setup<NC, P>(args, S, q, amax, fmax, err, qa, &nfrc, rank);
         if (nact < 0) continue;   // both CTAs see the same count
-        // ---- v_0 = e_q (registers, own rows, the partner's halo rows) ----
+        // ---- v_0 = e_q (own rows, the partner's halo rows; registers on the CUDA-core path) ----
         float vz[ZL];
         const int z0 = th.zh * G::ZS, len = th.zh ? NC - G::ZS : G::ZS;
 #pragma unroll
         for (int c = 0; c < ZL; c++) {
             vz[c] = (th.centre_xy && th.zh == mh && c == mc) ? 1.0f : 0.0f;
             if (th.live && c < len) {
-                S.U[((size_t)(z0 + c) * NR + th.row) * NC + th.a] = vz[c];
-                if (th.prow >= 0) U_remote[((size_t)(z0 + c) * NR + th.prow) * NC + th.a] = vz[c];
+                S.U[(size_t)(z0 + c) * G::PS + th.row * NC + th.a] = vz[c];
+                if (th.prow >= 0) U_remote[(size_t)(z0 + c) * G::PS + th.prow * NC + th.a] = vz[c];
             }
         }
         if (th.centre_xy && th.zh == mh) args.mu[q] = 1.0f;
+        __syncwarp();   // the tensor-core dots read the warp's own rows of v_0
         const float *drow = args.dpad + (size_t)qa[2] * plane_p + (size_t)(qa[1] + (th.slab ? th.b : 0)) * args.pn[0] +
                             qa[0] + (th.live ? th.a : 0);
+        float *mu_out = (th.centre_xy && th.zh == mh) ? args.mu + q : nullptr;
 
-        for (int k = 0; k <= args.K; k++) {
-            const bool need_dots = k < args.K;
-            if (th.zh == 0) cluster_dots<NC, P, 0>(args, S, th, vz, need_dots, amax, fmax);
-            else cluster_dots<NC, P, 1>(args, S, th, vz, need_dots, amax, fmax);
-            __syncthreads();
-            cluster_slot_sums<NC, P>(args, S, part_remote, rank, k, need_dots, nact, nfrc, amax, fmax);
-            cluster.sync();   // X: partial dots of both CTAs, the halo rows and the other z half are visible
-            if (!need_dots) break;
-            for (int it = threadIdx.x; it < nact * 4; it += blockDim.x) S.sd[it] = S.part[it] + S.part[amax * 4 + it];
-            __syncthreads();
-            const float ca = k == 0 ? 1.f : 2.f, cb = k == 0 ? 0.f : 1.f;
-            float w[ZL];
-            if (th.zh == 0) cluster_local<NC, P, 0>(args, S, th, vz, w, drow, (int)plane_p);
-            else cluster_local<NC, P, 1>(args, S, th, vz, w, drow, (int)plane_p);
-            // Y (arrive): this CTA's reads of v_k's buffer are done
-            __syncwarp();
-            auto y_token = cluster.barrier_arrive();
-            if (th.zh == 0) cluster_kb<NC, P, 0>(S, th, w, kap0, kap1, amax);
-            else cluster_kb<NC, P, 1>(S, th, w, kap0, kap1, amax);
-            // Y (wait): both CTAs are done reading v_k's buffers
-            __syncwarp();
-            cluster.barrier_wait(std::move(y_token));
-            if (th.zh == 0) cluster_finish<NC, P, 0>(th, w, vz, own, rem, pv, ca, cb, k == 0);
-            else cluster_finish<NC, P, 1>(th, w, vz, own, rem, pv, ca, cb, k == 0);
-            if (th.centre_xy && th.zh == mh) args.mu[(size_t)(k + 1) * N_d + q] = vz[mc];
+        if constexpr (MMA) {
+            // the warp's atom list; a longer one than the path takes is reported (the host then redoes the
+            // launch on the CUDA-core path) and cut, so every index stays in range
+            int l0 = -1, l1 = -1, nL = 0;
+            if (th.slab) {
+                const int W = (amax + 31) / 32;
+                nL = th.zh == 0 ? warp_atom_list<0>(S, th.bl, W, th.lane, l0, l1)
+                                : warp_atom_list<1>(S, th.bl, W, th.lane, l0, l1);
+                if (nL > kMmaMaxList) {
+                    if (th.lane == 0) atomicExch(err, 3);
+                    nL = kMmaMaxList;
+                }
+            }
+            for (int k = 0; k <= args.K; k++) {
+                const bool need_dots = k < args.K;
+                if (need_dots) {
+                    if (th.zh == 0) cl_dots_mma<NC, P, 0>(S, th, l0, l1, nL, amax);
+                    else cl_dots_mma<NC, P, 1>(S, th, l0, l1, nL, amax);
+                }
+                if (args.want_force) {
+                    float vf[ZL];
+                    load_pencil<NC, P>(th, own, vf);
+                    if (th.zh == 0) cluster_dots<NC, P, 0>(args, S, th, vf, need_dots, false, amax, fmax);
+                    else cluster_dots<NC, P, 1>(args, S, th, vf, need_dots, false, amax, fmax);
+                }
+                __syncthreads();
+                cluster_slot_sums<NC, P>(args, S, part_remote, rank, k, need_dots, nact, nfrc, amax, fmax);
+                cluster.sync();   // X: partial dots of both CTAs, the halo rows and the other z half are visible
+                if (!need_dots) break;
+                for (int it = threadIdx.x; it < nact * 4; it += blockDim.x) S.sd[it] = S.part[it] + S.part[amax * 4 + it];
+                __syncthreads();
+                const float ca = k == 0 ? 1.f : 2.f, cb = k == 0 ? 0.f : 1.f;
+                float w[ZL];
+                {
+                    float vk[ZL];
+                    load_pencil<NC, P>(th, own, vk);
+                    if (th.zh == 0) {
+                        cluster_local<NC, P, 0>(args, S, th, vk, w, drow, (int)plane_p);
+                        cluster_prefinish<NC, P, 0>(th, w, vk, pv, ca, cb, k == 0);
+                    } else {
+                        cluster_local<NC, P, 1>(args, S, th, vk, w, drow, (int)plane_p);
+                        cluster_prefinish<NC, P, 1>(th, w, vk, pv, ca, cb, k == 0);
+                    }
+                }
+                // Y (arrive): this CTA's reads of v_k's buffer are done
+                __syncwarp();
+                auto y_token = cluster.barrier_arrive();
+                float acc[2][2][4];
+                if (th.zh == 0) cl_kb_mma<NC, P, 0>(S, th, l0, l1, nL, kap0, kap1, amax, acc);
+                else cl_kb_mma<NC, P, 1>(S, th, l0, l1, nL, kap0, kap1, amax, acc);
+                // Y (wait): both CTAs are done reading v_k's buffers
+                __syncwarp();
+                cluster.barrier_wait(std::move(y_token));
+                float *muk = mu_out ? mu_out + (size_t)(k + 1) * N_d : nullptr;
+                if (th.zh == 0) cluster_finish_mma<NC, P, 0>(S, th, w, acc, own, rem, ca, muk, mc);
+                else cluster_finish_mma<NC, P, 1>(S, th, w, acc, own, rem, ca, muk, mc);
+            }
+        } else {
+            for (int k = 0; k <= args.K; k++) {
+                const bool need_dots = k < args.K;
+                if (th.zh == 0) cluster_dots<NC, P, 0>(args, S, th, vz, need_dots, true, amax, fmax);
+                else cluster_dots<NC, P, 1>(args, S, th, vz, need_dots, true, amax, fmax);
+                __syncthreads();
+                cluster_slot_sums<NC, P>(args, S, part_remote, rank, k, need_dots, nact, nfrc, amax, fmax);
+                cluster.sync();   // X: partial dots of both CTAs, the halo rows and the other z half are visible
+                if (!need_dots) break;
+                for (int it = threadIdx.x; it < nact * 4; it += blockDim.x) S.sd[it] = S.part[it] + S.part[amax * 4 + it];
+                __syncthreads();
+                const float ca = k == 0 ? 1.f : 2.f, cb = k == 0 ? 0.f : 1.f;
+                float w[ZL];
+                if (th.zh == 0) cluster_local<NC, P, 0>(args, S, th, vz, w, drow, (int)plane_p);
+                else cluster_local<NC, P, 1>(args, S, th, vz, w, drow, (int)plane_p);
+                // Y (arrive): this CTA's reads of v_k's buffer are done
+                __syncwarp();
+                auto y_token = cluster.barrier_arrive();
+                if (th.zh == 0) cluster_kb<NC, P, 0>(S, th, w, kap0, kap1, amax);
+                else cluster_kb<NC, P, 1>(S, th, w, kap0, kap1, amax);
+                // Y (wait): both CTAs are done reading v_k's buffers
+                __syncwarp();
+                cluster.barrier_wait(std::move(y_token));
+                if (th.zh == 0) cluster_finish<NC, P, 0>(th, w, vz, own, rem, pv, ca, cb, k == 0);
+                else cluster_finish<NC, P, 1>(th, w, vz, own, rem, pv, ca, cb, k == 0);
+                if (mu_out) mu_out[(size_t)(k + 1) * N_d] = vz[mc];
+            }
         }
     }
     cluster.sync();   // no CTA leaves while its partner may still write into its shared memory
 }
 
-template <int NC, int P>
+template <int NC, int P, bool MMA>
 cudaError_t cluster_config(int amax, int fmax, size_t *smem, int *max_clusters)
 {
     using G = CGeo<NC, P>;
     const size_t sm = cluster_layout<NC, P>(nullptr, amax, fmax, nullptr);
     *smem = sm;
-    auto kern = cluster_kernel<NC, P>;
+    auto kern = cluster_kernel<NC, P, MMA>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -726,12 +1109,12 @@ cudaError_t cluster_config(int amax, int fmax, size_t *smem, int *max_clusters)
     return cudaOccupancyMaxActiveClusters(max_clusters, kern, &cfg);
 }
 
-template <int NC, int P>
+template <int NC, int P, bool MMA>
 cudaError_t cluster_launch(const RecursionArgs<float> &args, int amax, int fmax, int nclusters, size_t smem, int *err,
                            cudaStream_t stream)
 {
     using G = CGeo<NC, P>;
-    auto kern = cluster_kernel<NC, P>;
+    auto kern = cluster_kernel<NC, P, MMA>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -755,25 +1138,42 @@ cudaError_t cluster_launch(const RecursionArgs<float> &args, int amax, int fmax,
 
 long long cluster_scratch_floats(int nc)
 {
-    return nc == 29 ? (long long)CGeo<29, 6>::SCR : 0;
+    switch (nc) {
+    case 25: return (long long)CGeo<25, 6>::SCR;
+    case 29: return (long long)CGeo<29, 6>::SCR;
+    default: return 0;
+    }
 }
+
+// Cube sizes that take the cluster kernel (the 21^3 and 25^3 cubes run on the one-CTA slab kernel).
+static bool cluster_cube(int nc) { return nc == 29; }
 
 bool cluster_supported(const int nc[3], int fd_half)
 {
-    return nc[0] == nc[1] && nc[1] == nc[2] && nc[0] == 29 && fd_half == 6;
+    return nc[0] == nc[1] && nc[1] == nc[2] && cluster_cube(nc[0]) && fd_half == 6;
 }
 
-cudaError_t cluster_prepare(int nc, int amax, int fmax, size_t *smem, int *max_clusters)
+cudaError_t cluster_prepare(int nc, int amax, int fmax, int kb_fma, size_t *smem, int *max_clusters)
 {
-    if (nc != 29) return cudaErrorInvalidValue;
-    return cluster_config<29, 6>(amax, fmax, smem, max_clusters);
+    switch (nc) {
+    case 25: return kb_fma ? cluster_config<25, 6, false>(amax, fmax, smem, max_clusters)
+                           : cluster_config<25, 6, true>(amax, fmax, smem, max_clusters);
+    case 29: return kb_fma ? cluster_config<29, 6, false>(amax, fmax, smem, max_clusters)
+                           : cluster_config<29, 6, true>(amax, fmax, smem, max_clusters);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_cluster(const RecursionArgs<float> &args, int amax, int fmax, int nclusters, size_t smem, int *err,
                            cudaStream_t stream)
 {
-    if (args.nc[0] != 29) return cudaErrorInvalidValue;
-    return cluster_launch<29, 6>(args, amax, fmax, nclusters, smem, err, stream);
+    switch (args.nc[0]) {
+    case 25: return args.kb_fma ? cluster_launch<25, 6, false>(args, amax, fmax, nclusters, smem, err, stream)
+                                : cluster_launch<25, 6, true>(args, amax, fmax, nclusters, smem, err, stream);
+    case 29: return args.kb_fma ? cluster_launch<29, 6, false>(args, amax, fmax, nclusters, smem, err, stream)
+                                : cluster_launch<29, 6, true>(args, amax, fmax, nclusters, smem, err, stream);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace sq

@@ -117,6 +117,9 @@ struct sq_handle_s {
     size_t scratch_cap = 0;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int kernel_used = 0;            // 0: generic recursion kernel, 1: FP32 slab kernel, 2: FP32 cluster kernel
+                                    // (tensor-core projector term), 3: Lanczos kernel, 4: FP32 cluster kernel
+                                    // (CUDA-core projector term)
+    int kb_fma = 0;                 // SQ_KB_FMA of the last sq_density / sq_moments_range call
     float t_rec = 0, t_msum = 0, t_fermi = 0;
 };
 
@@ -905,6 +908,7 @@ static void fill_args(sq_handle h, int K, int want_force, RecursionArgs<T> &a)
     a.natom = h->natom;
     a.nproj = h->nproj;
     a.want_force = want_force;
+    a.kb_fma = h->kb_fma;
     if constexpr (sizeof(T) == 8) {
         a.dpad = reinterpret_cast<const T *>(h->d_dpad64);
         a.fac = reinterpret_cast<const T *>(h->d_fac2_64);
@@ -965,7 +969,7 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, long long q0,
             const int amax = cnt[0] > 0 ? cnt[0] : 1, fmax = cnt[1] > 0 ? cnt[1] : 1;
             size_t sm = 0;
             int maxc = 0;
-            if (cluster_prepare(h->nc[0], amax, fmax, &sm, &maxc) == cudaSuccess && sm <= (size_t)dev_smem &&
+            if (cluster_prepare(h->nc[0], amax, fmax, a.kb_fma, &sm, &maxc) == cudaSuccess && sm <= (size_t)dev_smem &&
                 maxc > 0) {
                 long long ncl = maxc;
                 if (ncl > q1 - q0) ncl = q1 - q0;
@@ -973,7 +977,7 @@ static sq_status run_recursion(sq_handle h, int K, int want_force, long long q0,
                                 sizeof(float) * (size_t)cluster_scratch_floats(h->nc[0]) * 2 * ncl)))
                     return s;
                 a.scratch = reinterpret_cast<T *>(h->d_scratch);
-                h->kernel_used = 2;
+                h->kernel_used = a.kb_fma ? 4 : 2;
                 SQ_CUDA(cudaEventRecord(h->ev[0], stream));
                 SQ_COUNT(1);
                 SQ_CUDA(launch_cluster(a, amax, fmax, (int)ncl, sm, d_cnt + 2, stream));
@@ -1313,28 +1317,37 @@ static sq_status moments_stage(sq_handle h, int K, int precision, int want_force
     if ((s = ensure(&h->d_mu, &h->mu_bytes, esz * (size_t)(K + 1) * h->N_d))) return s;
     if ((s = ensure(&h->d_msum, &h->msum_cap, sizeof(double) * (size_t)(K + 1)))) return s;
     if ((s = ensure(&h->d_msum_part, &h->part_cap, sizeof(double) * (size_t)(K + 1) * kSumBlocks))) return s;
-    if (want_force) {
-        const size_t abytes = sizeof(double) * (size_t)(K + 1) * h->natom * h->nproj * 3;
-        if ((s = ensure(&h->d_A, &h->A_cap, abytes))) return s;
-        SQ_CUDA(cudaMemsetAsync(h->d_A, 0, abytes, stream));
-    }
+    const size_t abytes = sizeof(double) * (size_t)(K + 1) * h->natom * h->nproj * 3;
+    if (want_force && (s = ensure(&h->d_A, &h->A_cap, abytes))) return s;
     h->precision = precision;
     h->K = K;
-    s = precision == SQ_FP64 ? run_recursion<double>(h, K, want_force, q0, q1, stream)
-                             : run_recursion<float>(h, K, want_force, q0, q1, stream);
-    if (s) return s;
-    int *d_bad = reinterpret_cast<int *>(h->d_small);
-    SQ_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), stream));
-    SQ_COUNT(1);
-    k_msum_final<<<1, 256, 0, stream>>>(h->d_msum_part, kSumBlocks, K, h->d_msum, d_bad);
-    SQ_CUDA(cudaGetLastError());
-    SQ_CUDA(cudaEventRecord(h->ev[2], stream));
     int bad = 0, slab_err = 0;
-    SQ_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    if (h->kernel_used != 0)
-        SQ_CUDA(cudaMemcpyAsync(&slab_err, reinterpret_cast<int *>(h->d_small) + 42, sizeof(int),
-                                cudaMemcpyDeviceToHost, stream));
-    SQ_CUDA(cudaStreamSynchronize(stream));
+    for (int attempt = 0; attempt < 2; attempt++) {
+        if (want_force) SQ_CUDA(cudaMemsetAsync(h->d_A, 0, abytes, stream));
+        s = precision == SQ_FP64 ? run_recursion<double>(h, K, want_force, q0, q1, stream)
+                                 : run_recursion<float>(h, K, want_force, q0, q1, stream);
+        if (s) return s;
+        int *d_bad = reinterpret_cast<int *>(h->d_small);
+        SQ_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), stream));
+        SQ_COUNT(1);
+        k_msum_final<<<1, 256, 0, stream>>>(h->d_msum_part, kSumBlocks, K, h->d_msum, d_bad);
+        SQ_CUDA(cudaGetLastError());
+        SQ_CUDA(cudaEventRecord(h->ev[2], stream));
+        bad = 0;
+        slab_err = 0;
+        SQ_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        if (h->kernel_used != 0)
+            SQ_CUDA(cudaMemcpyAsync(&slab_err, reinterpret_cast<int *>(h->d_small) + 42, sizeof(int),
+                                    cudaMemcpyDeviceToHost, stream));
+        SQ_CUDA(cudaStreamSynchronize(stream));
+        // a warp's atom list longer than the tensor-core projector path takes: redo the launch with the
+        // CUDA-core form of the projector term
+        if (slab_err == 3 && h->kernel_used == 2 && attempt == 0) {
+            h->kb_fma = 1;
+            continue;
+        }
+        break;
+    }
     if (slab_err) return fail(SQ_ERR_UNSUPPORTED, "a column exceeded the FP32 kernel's atom capacity (%d)", slab_err);
     if (bad) return fail(SQ_ERR_NOT_FINITE, "moment sums are not finite");
     SQ_CUDA(cudaEventElapsedTime(&h->t_rec, h->ev[0], h->ev[1]));
@@ -1352,7 +1365,7 @@ static sq_status check_density_args(sq_handle h, int K, double kT, double N_e, i
     if (!(kT > 0) || !std::isfinite(kT)) return fail(SQ_ERR_ARG, "kT = %g", kT);
     if (!(N_e > 0) || !(N_e < 2.0 * h->N_d)) return fail(SQ_ERR_ARG, "N_e = %g", N_e);
     if (precision != SQ_FP64 && precision != SQ_FP32) return fail(SQ_ERR_ARG, "precision %d", precision);
-    if (flags & ~(SQ_WANT_FORCE | SQ_GAUSS)) return fail(SQ_ERR_ARG, "flags %d", flags);
+    if (flags & ~(SQ_WANT_FORCE | SQ_GAUSS | SQ_KB_FMA)) return fail(SQ_ERR_ARG, "flags %d", flags);
     if ((flags & SQ_GAUSS) && (flags & SQ_WANT_FORCE))
         return fail(SQ_ERR_ARG, "SQ_GAUSS gives rho, U and S; the force moments need the Chebyshev path");
     if ((flags & SQ_GAUSS) && K > kGaussMaxK) return fail(SQ_ERR_ARG, "K = %d above the Gauss path's %d", K, kGaussMaxK);
@@ -1369,6 +1382,7 @@ extern "C" sq_status sq_density(sq_handle h, int K, double kT, double N_e, int p
     cudaStream_t stream = (cudaStream_t)stream_;
     if (flags & SQ_GAUSS) return gauss_density(h, K, kT, N_e, precision, d_rho, lambda_f, stream);
     h->gauss = 0;
+    h->kb_fma = (flags & SQ_KB_FMA) ? 1 : 0;
     const int want_force = (flags & SQ_WANT_FORCE) && h->natom > 0;
     if ((s = moments_stage(h, K, precision, want_force, 0, h->N_d, stream))) return s;
     if ((s = fermi_and_density(h, kT, N_e, d_rho, lambda_f, stream))) return s;
@@ -1400,7 +1414,7 @@ extern "C" sq_status sq_moments_range(sq_handle h, int K, int precision, int fla
     if (!h || !msum) return fail(SQ_ERR_ARG, "null argument");
     if (K < 1 || K > 4096) return fail(SQ_ERR_ARG, "K = %d", K);
     if (precision != SQ_FP64 && precision != SQ_FP32) return fail(SQ_ERR_ARG, "precision %d", precision);
-    if (flags & ~SQ_WANT_FORCE) return fail(SQ_ERR_ARG, "flags %d", flags);
+    if (flags & ~(SQ_WANT_FORCE | SQ_KB_FMA)) return fail(SQ_ERR_ARG, "flags %d", flags);
     if (q_begin < 0 || q_end > h->N_d || q_begin >= q_end)
         return fail(SQ_ERR_ARG, "column range [%lld, %lld) of %lld", q_begin, q_end, h->N_d);
     const int want_force = (flags & SQ_WANT_FORCE) && h->natom > 0;
@@ -1408,6 +1422,7 @@ extern "C" sq_status sq_moments_range(sq_handle h, int K, int precision, int fla
     cudaStream_t stream = (cudaStream_t)stream_;
     sq_status s;
     h->gauss = 0;
+    h->kb_fma = (flags & SQ_KB_FMA) ? 1 : 0;
     if ((s = moments_stage(h, K, precision, want_force, q_begin, q_end, stream))) return s;
     SQ_CUDA(cudaMemcpyAsync(msum, h->d_msum, sizeof(double) * (K + 1), cudaMemcpyDeviceToHost, stream));
     if (want_force)
@@ -1716,7 +1731,8 @@ extern "C" const char *sq_kernel_name(sq_handle h)
 {
     if (!h || !h->have_density) return "";
     if (h->kernel_used == 1) return h->nc[0] == 21 ? "slab_kernel<21,6>" : "slab_kernel<25,6>";
-    if (h->kernel_used == 2) return "cluster_kernel<29,6>";
+    if (h->kernel_used == 2) return h->nc[0] == 25 ? "cluster_kernel<25,6,mma>" : "cluster_kernel<29,6,mma>";
+    if (h->kernel_used == 4) return h->nc[0] == 25 ? "cluster_kernel<25,6,fma>" : "cluster_kernel<29,6,fma>";
     if (h->kernel_used == 3) return h->precision == SQ_FP64 ? "lanczos_kernel<double>" : "lanczos_kernel<float>";
     return h->precision == SQ_FP64 ? "recursion_kernel<double>" : "recursion_kernel<float>";
 }
@@ -1935,7 +1951,7 @@ extern "C" sq_status sq_batch_create(const sq_handle *cells, int ncells, const i
     g_last_error[0] = 0;
     if (!cells || !K || !kT || !N_e || !out || ncells < 1) return fail(SQ_ERR_ARG, "null argument or ncells < 1");
     if (precision != SQ_FP64 && precision != SQ_FP32) return fail(SQ_ERR_ARG, "precision %d", precision);
-    if (flags & ~SQ_WANT_FORCE) return fail(SQ_ERR_ARG, "flags %d", flags);
+    if (flags & ~(SQ_WANT_FORCE | SQ_KB_FMA)) return fail(SQ_ERR_ARG, "flags %d", flags);
     sq_batch_s *b = new sq_batch_s();
     auto cleanup = [&](sq_status s) {
         sq_batch_destroy(b);
@@ -1954,6 +1970,7 @@ extern "C" sq_status sq_batch_create(const sq_handle *cells, int ncells, const i
         int M = 1;
         while (M < need) M <<= 1;
         if (M > (1 << 26)) return cleanup(fail(SQ_ERR_UNSUPPORTED, "cell %d: kT/tau too small", i));
+        h->kb_fma = (flags & SQ_KB_FMA) ? 1 : 0;
         b->cells.push_back(h);
         b->K.push_back(K[i]);
         b->kT.push_back(kT[i]);
@@ -2171,7 +2188,7 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
                 size_t sm = 0;
                 int maxc = 0;
                 if (cl) {
-                    if (cluster_prepare(h->nc[0], amax, fmax, &sm, &maxc) != cudaSuccess || maxc < 1 ||
+                    if (cluster_prepare(h->nc[0], amax, fmax, args[i].kb_fma, &sm, &maxc) != cudaSuccess || maxc < 1 ||
                         sm > (size_t)dev_smem) {
                         cudaGetLastError();
                         continue;
@@ -2287,6 +2304,10 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
         if (h->kernel_used) {
             int slab_err = 0;
             SQ_CUDA(cudaMemcpy(&slab_err, reinterpret_cast<int *>(h->d_small) + 42, sizeof(int), cudaMemcpyDeviceToHost));
+            if (slab_err == 3)
+                return fail(SQ_ERR_UNSUPPORTED,
+                            "cell %d: a warp's atom list exceeds the tensor-core projector path; create the batch "
+                            "with SQ_KB_FMA", i);
             if (slab_err) return fail(SQ_ERR_UNSUPPORTED, "cell %d: a column exceeded the slab kernel's atom capacity", i);
         }
         if (fin.phase == 4)

@@ -28,6 +28,7 @@ struct RecursionArgs {
     int natom;
     int nproj;           // 1 (s) or 4 (s + p)
     int want_force;
+    int kb_fma;          // cluster kernel: projector term on the CUDA cores instead of the tensor cores
     // scaled operator Hhat = (H - omega)/tau
     const T *dpad;       // Hhat diagonal on the periodically padded grid [n3+2m3][n2+2m2][n1+2m1]
     int pn[3];           // padded extents
@@ -140,7 +141,7 @@ long long slab_vector_floats(int nc);
 // launch needs args.scratch with cluster_scratch_floats(nc) floats per CTA (2 per cluster).
 bool cluster_supported(const int nc[3], int fd_half);
 long long cluster_scratch_floats(int nc);
-cudaError_t cluster_prepare(int nc, int amax, int fmax, size_t *smem, int *max_clusters);
+cudaError_t cluster_prepare(int nc, int amax, int fmax, int kb_fma, size_t *smem, int *max_clusters);
 cudaError_t launch_cluster(const RecursionArgs<float> &args, int amax, int fmax, int nclusters, size_t smem,
                            int *err, cudaStream_t stream);
 

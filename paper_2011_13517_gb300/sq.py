@@ -20,6 +20,7 @@ SQ_FP64 = 0
 SQ_FP32 = 1
 SQ_WANT_FORCE = 1
 SQ_GAUSS = 2
+SQ_KB_FMA = 4
 SQ_GRAD_ANALYTIC = 0
 SQ_GRAD_FD = 1
 
@@ -412,13 +413,14 @@ def build_for_cell(cell, bounds=None, stream=None, d_veff=None, flags=SQ_GRAD_AN
 
 
 def solve_cell(cell, precision=SQ_FP64, force=True, bounds=None, K=None, kT=None, N_e=None, stream=None,
-               grad=SQ_GRAD_ANALYTIC):
-    """Build + density (+ energy, force) for one cell; returns numpy results."""
+               grad=SQ_GRAD_ANALYTIC, extra_flags=0):
+    """Build + density (+ energy, force) for one cell; returns numpy results.  extra_flags is or-ed into
+    sq_density's flags (SQ_KB_FMA)."""
     h = build_for_cell(cell, bounds=bounds, stream=stream, flags=grad)
     try:
         rho = torch.empty(cell.N_d, dtype=torch.float64, device="cuda")
         lam_f = sq_density(h, cell.K if K is None else K, cell.kT if kT is None else kT,
-                           cell.N_e if N_e is None else N_e, precision, SQ_WANT_FORCE if force else 0, rho,
+                           cell.N_e if N_e is None else N_e, precision, (SQ_WANT_FORCE if force else 0) | extra_flags, rho,
                            stream=stream)
         U, S, F = sq_energy(h, stream=stream)
         out = dict(lam_f=lam_f, U=U, S=S, F=F, bounds=sq_get_spectral_bounds(h))

@@ -280,20 +280,23 @@ def test_fp32_21_cube_matches_oracle():
     assert abs(gpu["lam_f"] - ref64["lam_f"]) < 1e-5
 
 
-def test_fp32_29_cube_cluster_matches_oracle():
-    """FP32 on 29^3 cubes (R_cut = 7 bohr), which run on the two-CTA cluster kernel: a 48-site cell
+@pytest.mark.parametrize("kb", ["mma", "fma"])
+def test_fp32_29_cube_cluster_matches_oracle(kb):
+    """FP32 on 29^3 cubes (R_cut = 7 bohr), which run on the two-CTA cluster kernel, with the projector
+    term on the tensor cores (3xTF32, the default) or on the CUDA cores (SQ_KB_FMA): a 48-site cell
     (36x42x39 grid) with a vacancy and an Al-like solute, K = 24.  Sampled moments against the oracle;
     every moment, rho, lambda_f and forces against the FP64 GPU path, whose moments are checked against
     the same oracle columns at 1e-12."""
     c = cells.make_cell("rc7", (3, 2, 2), 0.5, 12, 1, 7.0, 24, 0.005, seed=5, n_vacancy=1, n_al=1)
     assert np.all(c.n_c == 29)
+    extra = sq.SQ_KB_FMA if kb == "fma" else 0
     lo, hi = oracle.spectral_bounds(c)
-    g32 = sq.solve_cell(c, sq.SQ_FP32, force=True, bounds=(lo, hi))
+    g32 = sq.solve_cell(c, sq.SQ_FP32, force=True, bounds=(lo, hi), extra_flags=extra)
     g64 = sq.solve_cell(c, sq.SQ_FP64, force=True, bounds=(lo, hi))
     h = sq.build_for_cell(c, bounds=(lo, hi))
     rho = torch.empty(c.N_d, dtype=torch.float64, device="cuda")
-    sq.sq_density(h, 2, c.kT, c.N_e, sq.SQ_FP32, 0, rho)
-    assert sq.sq_kernel_name(h) == "cluster_kernel<29,6>"
+    sq.sq_density(h, 2, c.kT, c.N_e, sq.SQ_FP32, extra, rho)
+    assert sq.sq_kernel_name(h) == f"cluster_kernel<29,6,{kb}>"
     h.close()
     omega, tau = oracle.scale_shift(lo, hi)
     cols = cells.sample_columns(c, 48)
@@ -302,7 +305,7 @@ def test_fp32_29_cube_cluster_matches_oracle():
     err_o = float(np.max(np.abs(g32["mu"][:, cols].T - mu)))
     err_all = float(np.max(np.abs(g32["mu"] - g64["mu"])))
     e = fp32_errors(g32, dict(g64, mu=g64["mu"].T), c)
-    print("FP32 29^3 cluster kernel: max moment error vs oracle", err_o, "vs FP64 (all columns)", err_all, e)
+    print(f"FP32 29^3 cluster kernel ({kb}): max moment error vs oracle", err_o, "vs FP64 (all columns)", err_all, e)
     assert err_o < 1e-6 and err_all < 1e-6
     assert e["dlam"] < 1e-6 and e["rho_max_rel"] < 1e-5 and e["dU_per_atom"] < 1e-5 and e["df_max"] < 1e-6
     dV = float(np.prod(c.h))
