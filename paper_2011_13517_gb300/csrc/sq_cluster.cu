@@ -79,9 +79,10 @@ struct CSmem {
     float *fa;         // [2 amax][FAS] x factor rows: row 2t = g, row 2t+1 = hp of active atom t, zero past NC
     float2 *ty;        // [amax+1][NB0]  (g, hp) along y, own slabs
     float4 *tz;        // [2][amax+1][NZP] per z half: (g[z], hp[z], g[z+1], hp[z+1]) from the half's first z
-    float2 *fx;        // [fmax][NC]   (g', hp') of force atoms
+    float *fd;         // [2 (fmax+1)][FAS] x derivative rows (g', hp') of force slot fi, zero past NC; the
+                       // rows of slot fmax stay zero
     float2 *fy;        // [fmax][NB0]
-    float4 *fz;        // [2][fmax][NZP]
+    float4 *fz;        // [2][fmax+1][NZP] (g', hp') pairs along z per half; entry fmax stays zero
     float *slot;       // [NB0][2][amax][4] per (slab, z half)
     float *fslot;      // [NB0][2][fmax][12]
     float *part;       // [2][amax][4]: partial dots of rank 0 and rank 1 (each written by its rank)
@@ -121,9 +122,9 @@ __host__ __device__ inline size_t cluster_layout(unsigned char *base, int amax, 
     p = take(sizeof(float) * (size_t)2 * (amax + 1) * FAS);    if (s) s->fa = (float *)p;
     p = take(sizeof(float2) * (size_t)(amax + 1) * G::NB0);    if (s) s->ty = (float2 *)p;
     p = take(sizeof(float4) * (size_t)2 * (amax + 1) * G::NZP); if (s) s->tz = (float4 *)p;
-    p = take(sizeof(float2) * (size_t)fmax * NC);              if (s) s->fx = (float2 *)p;
+    p = take(sizeof(float) * (size_t)2 * (fmax + 1) * FAS);    if (s) s->fd = (float *)p;
     p = take(sizeof(float2) * (size_t)fmax * G::NB0);          if (s) s->fy = (float2 *)p;
-    p = take(sizeof(float4) * (size_t)2 * fmax * G::NZP);      if (s) s->fz = (float4 *)p;
+    p = take(sizeof(float4) * (size_t)2 * (fmax + 1) * G::NZP); if (s) s->fz = (float4 *)p;
     p = take(sizeof(float) * (size_t)G::NB0 * 2 * amax * 4);   if (s) s->slot = (float *)p;
     p = take(sizeof(float) * (size_t)G::NB0 * 2 * fmax * 12);  if (s) s->fslot = (float *)p;
     p = take(sizeof(float) * (size_t)2 * amax * 4);            if (s) s->part = (float *)p;
@@ -301,10 +302,13 @@ __device__ int cluster_setup(const RecursionArgs<float> &args, const CSmem &S, l
             return -1;
         }
         __syncthreads();
-        for (int it = threadIdx.x; it < nfrc * NC; it += NTH) {
-            const int o = it % NC, fi = it / NC;
-            const float *f0 = args.fac + (size_t)S.rec[S.ftl[fi]].J * args.fac_stride + args.fac_off[0] + wstart[0] + o;
-            S.fx[it] = make_float2(f0[4 * args.n[0]], f0[6 * args.n[0]]);
+        for (int it = threadIdx.x; it < nfrc * 2 * FAS; it += NTH) {
+            const int o = it % FAS, row = it / FAS;
+            float v = 0.f;
+            if (o < NC)
+                v = args.fac[(size_t)S.rec[S.ftl[row >> 1]].J * args.fac_stride + args.fac_off[0] + wstart[0] + o +
+                             (4 + 2 * (row & 1)) * args.n[0]];
+            S.fd[it] = v;
         }
         for (int it = threadIdx.x; it < nfrc * NB0; it += NTH) {
             const int o = it % NB0, fi = it / NB0;
@@ -323,7 +327,7 @@ __device__ int cluster_setup(const RecursionArgs<float> &args, const CSmem &S, l
             const int J = S.rec[S.ftl[fi]].J;
             const float2 u = z < zend ? zfac(J, z, 4) : make_float2(0.f, 0.f);
             const float2 v = z + 1 < zend ? zfac(J, z + 1, 4) : make_float2(0.f, 0.f);
-            S.fz[((size_t)h * fmax + fi) * NZP + i] = make_float4(u.x, u.y, v.x, v.y);
+            S.fz[((size_t)h * (fmax + 1) + fi) * NZP + i] = make_float4(u.x, u.y, v.x, v.y);
         }
     }
     for (int it = threadIdx.x; it < NB0 * W; it += NTH) {
@@ -512,16 +516,48 @@ __device__ __forceinline__ int warp_atom_list(const CSmem &S, int bl, int W, int
     return n;
 }
 
+// The force atoms (projectors nonzero at the column's centre) among the warp's list: lane j holds the
+// atom index of entry j (-1 past the end).  Returns the count; a count above 32 is cut to 32 with
+// error 3 (the host then redoes the launch on the CUDA-core path).
+template <int H>
+__device__ __forceinline__ int warp_force_list(const CSmem &S, int bl, int W, int lane, int &lf, int *err)
+{
+    int n = 0;
+    lf = -1;
+    for (int wd = 0; wd < W; wd++) {
+        const unsigned msk = S.ymask[bl * W + wd] & S.zmask[H * W + wd] & S.fbits[wd];
+        const int c = __popc(msk);
+        const int r = lane - n;
+        if (r >= 0 && r < c) {
+            unsigned mm = msk;
+            for (int i = 0; i < r; i++) mm &= mm - 1u;
+            lf = 32 * wd + __ffs(mm) - 1;
+        }
+        n += c;
+    }
+    if (n > 32) {
+        if (lane == 0) atomicExch(err, 3);
+        n = 32;
+    }
+    return n;
+}
+
 // Projector dots of every atom in the warp's list (nL <= kMmaMaxList) into the warp's slots, from v_k
-// in the warp's own rows of U.
+// in the warp's own rows of U.  With want_force also the force moments of the force atoms in the list
+// (lf, nF): the rows g and hp of a force atom take two more z sums (with g'_z and hp'_z), and extra
+// 16-row tiles carry the x derivative rows g' and hp' of the force atoms, so every one of the twelve
+// contractions (d_d chi_lm)^T v of a force atom comes out of the same MMAs.
 template <int NC, int P, int H>
-__device__ __forceinline__ void cl_dots_mma(const CSmem &S, const CThread<NC, P> &th, int l0, int l1, int nL, int amax)
+__device__ __forceinline__ void cl_dots_mma(const CSmem &S, const CThread<NC, P> &th, int l0, int l1, int nL, int lf,
+                                            int nF, int amax, int fmax, bool want_force, bool write_dots)
 {
     using G = CGeo<NC, P>;
     constexpr int NR = G::NR, NZP = G::NZP, NB0 = G::NB0, Z0 = ZHalf<NC, P, H>::Z0, LEN = ZHalf<NC, P, H>::LEN;
     const int g = th.lane >> 2, t = th.lane & 3;
     const float4 *tzh = S.tz + (size_t)H * (amax + 1) * NZP;
+    const float4 *fzh = S.fz + (size_t)H * (fmax + 1) * NZP;
     float *slot = S.slot + ((size_t)th.bl * 2 + H) * amax * 4;
+    float *fslot = S.fslot + ((size_t)th.bl * 2 + H) * fmax * 12;
     const float *urow = S.U + (size_t)th.row * NC;   // (z 0, own row, x 0)
     for (int mt = 0; 8 * mt < nL; mt++) {
         const int src = mt < 4 ? l0 : l1;
@@ -557,7 +593,107 @@ __device__ __forceinline__ void cl_dots_mma(const CSmem &S, const CThread<NC, P>
                 mma3(acc[nt], ah, al, bh, bo);
             }
         }
-        // z factors of the lane's two rows (z = 8 nt + 2t and 8 nt + 2t + 1 of the half)
+        // z factors of the lane's two rows (z = 8 nt + 2t and 8 nt + 2t + 1 of the half): sums with g_z
+        // and hp_z, and for force atoms with g'_z and hp'_z (slot fmax: zeros)
+        const int fA = want_force && okA ? S.rec[tA].fidx : -1, fB = want_force && okB ? S.rec[tB].fidx : -1;
+        const int zA = fA >= 0 ? fA : fmax, zB = fB >= 0 ? fB : fmax;
+        float sA1 = 0.f, sA2 = 0.f, sB1 = 0.f, sB2 = 0.f, sA3 = 0.f, sA4 = 0.f, sB3 = 0.f, sB4 = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++) {
+            const float4 pa = tzh[tA * NZP + 4 * nt + t], pb = tzh[tB * NZP + 4 * nt + t];
+            sA1 += pa.x * acc[nt][0] + pa.z * acc[nt][1];
+            sA2 += pa.y * acc[nt][0] + pa.w * acc[nt][1];
+            sB1 += pb.x * acc[nt][2] + pb.z * acc[nt][3];
+            sB2 += pb.y * acc[nt][2] + pb.w * acc[nt][3];
+            if (want_force) {
+                const float4 qa = fzh[zA * NZP + 4 * nt + t], qb = fzh[zB * NZP + 4 * nt + t];
+                sA3 += qa.x * acc[nt][0] + qa.z * acc[nt][1];
+                sA4 += qa.y * acc[nt][0] + qa.w * acc[nt][1];
+                sB3 += qb.x * acc[nt][2] + qb.z * acc[nt][3];
+                sB4 += qb.y * acc[nt][2] + qb.w * acc[nt][3];
+            }
+        }
+        // sum over the four lanes of a row pair (they hold different z)
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            sA1 += __shfl_xor_sync(0xffffffffu, sA1, o);
+            sA2 += __shfl_xor_sync(0xffffffffu, sA2, o);
+            sB1 += __shfl_xor_sync(0xffffffffu, sB1, o);
+            sB2 += __shfl_xor_sync(0xffffffffu, sB2, o);
+            if (want_force) {
+                sA3 += __shfl_xor_sync(0xffffffffu, sA3, o);
+                sA4 += __shfl_xor_sync(0xffffffffu, sA4, o);
+                sB3 += __shfl_xor_sync(0xffffffffu, sB3, o);
+                sB4 += __shfl_xor_sync(0xffffffffu, sB4, o);
+            }
+        }
+        // row g: x factor g (g even) or hp (g odd) of atom A; row g + 8 likewise of atom B
+        if (t < 2 && (t == 0 ? okA : okB)) {
+            const int at = t == 0 ? tA : tB, fi = t == 0 ? fA : fB;
+            const float s1 = t == 0 ? sA1 : sB1, s2 = t == 0 ? sA2 : sB2;
+            const float s3 = t == 0 ? sA3 : sB3, s4 = t == 0 ? sA4 : sB4;
+            const float2 yv = S.ty[at * NB0 + th.bl];
+            float *sl = slot + at * 4;
+            if ((g & 1) == 0) {
+                if (write_dots) {
+                    sl[0] = yv.x * s1;   // s
+                    sl[2] = yv.y * s1;   // p_y
+                    sl[3] = yv.x * s2;   // p_z
+                }
+                if (fi >= 0) {
+                    const float2 yd = S.fy[fi * NB0 + th.bl];
+                    float *fs = fslot + fi * 12;
+                    fs[1] = yd.x * s1;    // s d/dy
+                    fs[7] = yd.y * s1;    // p_y d/dy
+                    fs[10] = yd.x * s2;   // p_z d/dy
+                    fs[2] = yv.x * s3;    // s d/dz
+                    fs[8] = yv.y * s3;    // p_y d/dz
+                    fs[11] = yv.x * s4;   // p_z d/dz
+                }
+            } else {
+                if (write_dots) sl[1] = yv.x * s1;   // p_x
+                if (fi >= 0) {
+                    const float2 yd = S.fy[fi * NB0 + th.bl];
+                    float *fs = fslot + fi * 12;
+                    fs[4] = yd.x * s1;    // p_x d/dy
+                    fs[5] = yv.x * s3;    // p_x d/dz
+                }
+            }
+        }
+    }
+    if (!want_force) return;
+    // x derivative rows of the force atoms: row g of a tile is g' (g even) or hp' (g odd) of force atom
+    // 8 mt + g/2, row g + 8 of force atom 8 mt + 4 + g/2
+    for (int mt = 0; 8 * mt < nF; mt++) {
+        const int iA = 8 * mt + (g >> 1), iB = iA + 4;
+        const bool okA = iA < nF, okB = iB < nF;
+        const int sA = __shfl_sync(0xffffffffu, lf, iA & 31), sB = __shfl_sync(0xffffffffu, lf, iB & 31);
+        const int tA = okA ? sA : amax, tB = okB ? sB : amax;
+        const int fA = okA ? S.rec[sA].fidx : fmax, fB = okB ? S.rec[sB].fidx : fmax;
+        const float *rA = S.fd + (size_t)(2 * fA + (g & 1)) * FAS;
+        const float *rB = S.fd + (size_t)(2 * fB + (g & 1)) * FAS;
+        float acc[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+            for (int i = 0; i < 4; i++) acc[nt][i] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < 4; ks++) {
+            const int x0 = 8 * ks + t, x1 = x0 + 4;
+            unsigned ah[4], al[4];
+            split_tf32(rA[x0], ah[0], al[0]);
+            split_tf32(rB[x0], ah[1], al[1]);
+            split_tf32(rA[x1], ah[2], al[2]);
+            split_tf32(rB[x1], ah[3], al[3]);
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++) {
+                const float *col = urow + (size_t)(Z0 + 8 * nt + g) * CGeo<NC, P>::PS;
+                unsigned bh[2], bo[2];
+                split_tf32(col[x0], bh[0], bo[0]);
+                split_tf32(col[x1], bh[1], bo[1]);
+                mma3(acc[nt], ah, al, bh, bo);
+            }
+        }
         float sA1 = 0.f, sA2 = 0.f, sB1 = 0.f, sB2 = 0.f;
 #pragma unroll
         for (int nt = 0; nt < 2; nt++) {
@@ -567,7 +703,6 @@ __device__ __forceinline__ void cl_dots_mma(const CSmem &S, const CThread<NC, P>
             sB1 += pb.x * acc[nt][2] + pb.z * acc[nt][3];
             sB2 += pb.y * acc[nt][2] + pb.w * acc[nt][3];
         }
-        // sum over the four lanes of a row pair (they hold different z)
 #pragma unroll
         for (int o = 1; o <= 2; o <<= 1) {
             sA1 += __shfl_xor_sync(0xffffffffu, sA1, o);
@@ -575,18 +710,17 @@ __device__ __forceinline__ void cl_dots_mma(const CSmem &S, const CThread<NC, P>
             sB1 += __shfl_xor_sync(0xffffffffu, sB1, o);
             sB2 += __shfl_xor_sync(0xffffffffu, sB2, o);
         }
-        // row g: x factor g (g even) or hp (g odd) of atom A; row g + 8 likewise of atom B
         if (t < 2 && (t == 0 ? okA : okB)) {
-            const int at = t == 0 ? tA : tB;
+            const int at = t == 0 ? tA : tB, fi = t == 0 ? fA : fB;
             const float s1 = t == 0 ? sA1 : sB1, s2 = t == 0 ? sA2 : sB2;
             const float2 yv = S.ty[at * NB0 + th.bl];
-            float *sl = slot + at * 4;
+            float *fs = fslot + fi * 12;
             if ((g & 1) == 0) {
-                sl[0] = yv.x * s1;   // s
-                sl[2] = yv.y * s1;   // p_y
-                sl[3] = yv.x * s2;   // p_z
+                fs[0] = yv.x * s1;   // s d/dx
+                fs[6] = yv.y * s1;   // p_y d/dx
+                fs[9] = yv.x * s2;   // p_z d/dx
             } else {
-                sl[1] = yv.x * s1;   // p_x
+                fs[3] = yv.x * s1;   // p_x d/dx
             }
         }
     }
@@ -669,7 +803,7 @@ __device__ __forceinline__ void cluster_dots(const RecursionArgs<float> &args, c
     const bool live = th.live;
     if (!th.slab || !(need_dots || args.want_force)) return;
     const float4 *tzh = S.tz + (size_t)H * (amax + 1) * NZP;
-    const float4 *fzh = S.fz + (size_t)H * fmax * NZP;
+    const float4 *fzh = S.fz + (size_t)H * (fmax + 1) * NZP;
     float *slot = S.slot + ((size_t)bl * 2 + H) * amax * 4;
     float *fslot = S.fslot + ((size_t)bl * 2 + H) * fmax * 12;
     for (int wd = 0; wd < W; wd++) {
@@ -703,7 +837,8 @@ __device__ __forceinline__ void cluster_dots(const RecursionArgs<float> &args, c
             const float2 xv = xfac(S, t, a, live);
             const float2 yv = S.ty[t * NB0 + bl];
             float *sl = slot + t * 4;
-            const float2 xd = live ? S.fx[fidx * NC + a] : make_float2(0.f, 0.f);
+            const float2 xd = live ? make_float2(S.fd[2 * fidx * FAS + a], S.fd[(2 * fidx + 1) * FAS + a])
+                                   : make_float2(0.f, 0.f);
             const float2 yd = S.fy[fidx * NB0 + bl];
             const float v8[8] = {xv.x * Gs, xv.y * Gs, xv.x * Hs, xd.x * Gs, xv.x * Gd, xd.y * Gs, xv.y * Gd, xd.x * Hs};
             const float red = reduce8(v8, lane);
@@ -974,6 +1109,9 @@ __global__ void __launch_bounds__(CGeo<NC, P>::NW * 32, 1) cluster_kernel(const 
     for (int i = threadIdx.x; i < 2 * NZP; i += blockDim.x)
         S.tz[((size_t)(i / NZP) * (amax + 1) + amax) * NZP + i % NZP] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = threadIdx.x; i < 4; i += blockDim.x) S.sd[4 * amax + i] = 0.f;
+    for (int i = threadIdx.x; i < 2 * FAS; i += blockDim.x) S.fd[2 * fmax * FAS + i] = 0.f;
+    for (int i = threadIdx.x; i < 2 * NZP; i += blockDim.x)
+        S.fz[((size_t)(i / NZP) * (fmax + 1) + fmax) * NZP + i % NZP] = make_float4(0.f, 0.f, 0.f, 0.f);
     cluster.sync();   // both CTAs are running before any write into the partner's shared memory
 
     for (long long q = args.q0 + cid; q < args.q1; q += ncl) {
@@ -1000,7 +1138,7 @@ __global__ void __launch_bounds__(CGeo<NC, P>::NW * 32, 1) cluster_kernel(const 
         if constexpr (MMA) {
             // the warp's atom list; a longer one than the path takes is reported (the host then redoes the
             // launch on the CUDA-core path) and cut, so every index stays in range
-            int l0 = -1, l1 = -1, nL = 0;
+            int l0 = -1, l1 = -1, nL = 0, lf = -1, nF = 0;
             if (th.slab) {
                 const int W = (amax + 31) / 32;
                 nL = th.zh == 0 ? warp_atom_list<0>(S, th.bl, W, th.lane, l0, l1)
@@ -1009,18 +1147,16 @@ __global__ void __launch_bounds__(CGeo<NC, P>::NW * 32, 1) cluster_kernel(const 
                     if (th.lane == 0) atomicExch(err, 3);
                     nL = kMmaMaxList;
                 }
+                if (args.want_force)
+                    nF = th.zh == 0 ? warp_force_list<0>(S, th.bl, W, th.lane, lf, err)
+                                    : warp_force_list<1>(S, th.bl, W, th.lane, lf, err);
             }
             for (int k = 0; k <= args.K; k++) {
                 const bool need_dots = k < args.K;
-                if (need_dots) {
-                    if (th.zh == 0) cl_dots_mma<NC, P, 0>(S, th, l0, l1, nL, amax);
-                    else cl_dots_mma<NC, P, 1>(S, th, l0, l1, nL, amax);
-                }
-                if (args.want_force) {
-                    float vf[ZL];
-                    load_pencil<NC, P>(th, own, vf);
-                    if (th.zh == 0) cluster_dots<NC, P, 0>(args, S, th, vf, need_dots, false, amax, fmax);
-                    else cluster_dots<NC, P, 1>(args, S, th, vf, need_dots, false, amax, fmax);
+                if (need_dots || args.want_force) {
+                    const bool wf = args.want_force != 0;
+                    if (th.zh == 0) cl_dots_mma<NC, P, 0>(S, th, l0, l1, nL, lf, nF, amax, fmax, wf, need_dots);
+                    else cl_dots_mma<NC, P, 1>(S, th, l0, l1, nL, lf, nF, amax, fmax, wf, need_dots);
                 }
                 __syncthreads();
                 cluster_slot_sums<NC, P>(args, S, part_remote, rank, k, need_dots, nact, nfrc, amax, fmax);
