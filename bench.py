@@ -38,8 +38,13 @@ FP32_UNIT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # FP64: the nominal GB300 rate (1.25 TFLOP/s)
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) of one full-size launch, from one ncu capture of the same kernel version;
-# a kernel without a capture of its current version reports null
-MEASURED_TRAFFIC = {}
+# a kernel without a capture of its current version reports null.  cluster_kernel<29,6,mma>: the
+# K = 8 precision-cell launch read 8.98 MB and wrote 148.51 MB (register spills that leave L1, and
+# the moments); both scale with the recursion steps per column, so the K = 80 launch is taken as
+# 81/9 of that (an upper bound: the per-column set-up reads do not grow with K)
+MEASURED_TRAFFIC = {"cluster_kernel<29,6,mma>": (8.97536e6 + 148.50688e6) * 81 / 9}
+TRAFFIC_NOTE = {"cluster_kernel<29,6,mma>": "ncu capture of the K = 8 launch (157.5 MB) scaled by 81/9 column-steps; "
+                                            "upper bound"}
 
 
 DESCRIPTION = {
@@ -604,7 +609,8 @@ def main():
         ach = fb / (r["rec_ms"] * 1e-3) / 1e12
         ach_box = fx / (r["rec_ms"] * 1e-3) / 1e12
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": MEASURED_TRAFFIC.get(r["kernel"]), "kernel": r["kernel"], "kernel_ms": r["rec_ms"],
+                "traffic": MEASURED_TRAFFIC.get(r["kernel"]), "traffic_note": TRAFFIC_NOTE.get(r["kernel"]),
+                "kernel": r["kernel"], "kernel_ms": r["rec_ms"],
                 "count": "ball supports r < r_c (the hot-path measurement plan's count)",
                 "algorithmic_tflop_per_launch": fb / 1e12,
                 "achieved_box_count": ach_box, "frac_box_count": ach_box / peak,
