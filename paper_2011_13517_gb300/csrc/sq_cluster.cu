@@ -65,6 +65,8 @@ struct CGeo {
     // z planes of the buffer: the cube plus zero planes that the tensor-core path's whole 16-z tiles
     // of the upper half reach
     static constexpr int NZU = NC > ZS + 16 ? NC : ZS + 16;
+    // the tensor-core fragment loads read x up to 31 in the last row of a plane and z up to ZS + 15
+    static_assert(PS >= NR * NC && PS >= (NR - 1) * NC + 32 && PS % 32 == 4 && NZU >= ZS + 16, "buffer padding");
     static_assert(NC <= 32 && NC - NB0 + P <= NR && 2 * ZS >= NC && ZL <= 2 * NZP, "layout");
 };
 template <int NC, int P, int H>
