@@ -2231,7 +2231,7 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
     // autotune once: kernel configuration x work-item size, timed on a prefix of the work queue
     if (b->config < 0) {
         SQ_CUDA(cudaStreamSynchronize(stream));
-        const int configs[3] = {0, 1, 2};
+        const int cfg_list[3] = {0, 1, 2};
         const int chunks[2] = {32, 128};
         float best = 1e30f;
         int bc = -1, bk = 128;
@@ -2245,11 +2245,11 @@ static sq_status batch_run(sq_batch b, double *const *d_rho, double *lambda_f, c
                     if (b->slab_amax[i] == 0) total += b->cells[i]->N_d;
                 long long cols = std::min<long long>((long long)b->cells[0]->num_sms * 2 * 128, total / 6);
                 const int probe = (int)std::max<long long>(1, cols / chunks[ki]);
-                if (batch_enqueue<T>(b, args.data(), d_rho, b->cap_stream, configs[ci], chunks[ki], probe, &ms) != SQ_OK)
+                if (batch_enqueue<T>(b, args.data(), d_rho, b->cap_stream, cfg_list[ci], chunks[ki], probe, &ms) != SQ_OK)
                     continue;
                 if (ms < best) {
                     best = ms;
-                    bc = configs[ci];
+                    bc = cfg_list[ci];
                     bk = chunks[ki];
                 }
             }
