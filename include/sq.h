@@ -422,6 +422,41 @@ sq_status sq_batch_info(sq_batch b, int *config, int *chunk, int *grid, double *
 /* Release a batch (NULL is ignored; the cell handles are not touched). */
 void sq_batch_destroy(sq_batch b);
 
+/*
+ * Self-consistency pieces around the density (Sec. 2.1: LDA exchange-correlation, Eq. Poisson;
+ * Sec. 3 "Electrostatic and effective potential": V_eff^q = V_xc(rho^q) + phi^q).  All FP64 device
+ * arrays of one periodic grid [n3][n2][n1] (x fastest), caller-owned; each call synchronises `stream`.
+ *
+ * sq_lda_pw92 -- local exchange-correlation energy per electron eps_xc(rho) and potential
+ *   V_xc = d(rho eps_xc)/d rho: Slater exchange and the spin-unpolarised Perdew-Wang correlation
+ *   (published fit, p = 1); zero where rho <= 0.  n >= 1 points.  Errors: SQ_ERR_ARG, SQ_ERR_CUDA.
+ *
+ * sq_pseudocharge -- total pseudocharge of the nuclei on the grid of `box` (bohr) with n points per
+ *   axis: b(x) = sum_J -Z_J (2 pi sigma_b^2)^(-3/2) exp(-|x - R_J|^2 / (2 sigma_b^2)), minimum-image
+ *   distances (valid for boxes at least 12 sigma_b wide).  R: host [natom][3] bohr, Z: host [natom]
+ *   valence charges; natom >= 0.  Errors: SQ_ERR_ARG, SQ_ERR_NOT_FINITE, SQ_ERR_OOM, SQ_ERR_CUDA.
+ *
+ * sq_poisson_periodic -- phi with -(1/4 pi) L_h phi = f - mean(f) and mean(phi) = 0, L_h the periodic
+ *   finite-difference Laplacian of order fd_order (the kinetic term's stencil), by conjugate
+ *   gradients on -L_h until the residual is tol times that of phi = 0 (at most max_iter iterations).
+ *   The mean of f (a periodic cell's net charge) is removed: the periodic problem has no solution
+ *   otherwise.  Outputs the iteration count and the final relative residual.  Errors: SQ_ERR_ARG,
+ *   SQ_ERR_NOT_FINITE, SQ_ERR_TIMEOUT (not converged; phi holds the last iterate), SQ_ERR_OOM,
+ *   SQ_ERR_CUDA.  Allocates and frees its own work space (3 N + 256 doubles).
+ *
+ * sq_effective_potential -- the step from a density to the next effective potential: phi of
+ *   rho + b (as sq_poisson_periodic), eps_xc and V_xc of rho (as sq_lda_pw92) and V_eff = V_xc + phi.
+ *   Errors as sq_poisson_periodic.
+ */
+sq_status sq_lda_pw92(long long n, const double *d_rho, double *d_exc, double *d_vxc, void *stream);
+sq_status sq_pseudocharge(const int n[3], const double box[3], int natom, const double *R, const double *Z,
+                          double sigma_b, double *d_b, void *stream);
+sq_status sq_poisson_periodic(const int n[3], const double box[3], int fd_order, const double *d_f, double tol,
+                              int max_iter, double *d_phi, int *iters, double *rel_res, void *stream);
+sq_status sq_effective_potential(const int n[3], const double box[3], int fd_order, const double *d_rho,
+                                 const double *d_b, double tol, int max_iter, double *d_phi, double *d_exc,
+                                 double *d_vxc, double *d_veff, int *iters, double *rel_res, void *stream);
+
 /* Release a handle and its device workspace (NULL is ignored).  Synchronises the device. */
 void sq_destroy(sq_handle h);
 

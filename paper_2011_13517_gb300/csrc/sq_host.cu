@@ -2516,3 +2516,198 @@ extern "C" sq_status sq_density_vjp(sq_handle h, const double *d_rho_bar, double
     return h->precision == SQ_FP64 ? density_vjp<double>(h, d_rho_bar, U_bar, checkpoint_k, d_veff_bar, stream)
                                    : density_vjp<float>(h, d_rho_bar, U_bar, checkpoint_k, d_veff_bar, stream);
 }
+
+// ------------------------------------------------------------------------------------------------
+// Self-consistency pieces around the density (Sec. 2.1 LDA and Eq. Poisson; Sec. 3 "Electrostatic
+// and effective potential"): V_xc, pseudocharges, the periodic FD Poisson solve, V_eff = V_xc + phi.
+
+namespace {
+
+int current_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// device buffer freed on every return path
+struct DevBuf {
+    double *p = nullptr;
+    ~DevBuf()
+    {
+        if (p) cudaFree(p);
+    }
+};
+
+sq_status check_grid(const int n[3], const double box[3])
+{
+    if (!n || !box) return fail(SQ_ERR_ARG, "null grid");
+    for (int a = 0; a < 3; a++)
+        if (n[a] < 1 || !(box[a] > 0) || !std::isfinite(box[a]))
+            return fail(SQ_ERR_ARG, "axis %d: n = %d, box = %g", a, n[a], box[a]);
+    return SQ_OK;
+}
+
+// a.b (sum of a when b is null) in a fixed order: per-block partial sums, added on the host in order
+sq_status dot_fixed(long long N, const double *a, const double *b, double *d_part, cudaStream_t stream, double *out)
+{
+    double part[kDotBlocks];
+    SQ_COUNT(1);
+    SQ_CUDA(sq::launch_dot_partial(N, a, b, d_part, stream));
+    SQ_CUDA(cudaMemcpyAsync(part, d_part, sizeof(part), cudaMemcpyDeviceToHost, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    double s = 0.0;
+    for (int i = 0; i < kDotBlocks; i++) s += part[i];
+    *out = s;
+    return SQ_OK;
+}
+
+// -(1/4 pi) L_h phi = f - mean(f), mean(phi) = 0, by conjugate gradients on -L_h (symmetric positive
+// definite on zero-mean grid functions); work: 3 N + kDotBlocks doubles.
+sq_status poisson_cg(const int n[3], const double box[3], int fd_order, const double *d_f, double tol, int max_iter,
+                     double *d_phi, double *work, int *iters, double *rel_res, cudaStream_t stream)
+{
+    const long long N = (long long)n[0] * n[1] * n[2];
+    const int sms = current_sms();
+    sq::LapWeights w;
+    double c[kMaxHalfWidth + 1] = {0};
+    fd_coefficients(fd_order, c);
+    w.p = fd_order / 2;
+    for (int a = 0; a < 3; a++) {
+        const double ha = box[a] / n[a];
+        for (int d = 0; d <= kMaxHalfWidth; d++) w.c[a][d] = d <= w.p ? c[d] / (ha * ha) : 0.0;
+    }
+    double *r = work, *p = work + N, *Ap = work + 2 * N, *part = work + 3 * N;
+    const double four_pi = 4.0 * 3.14159265358979323846;
+    sq_status s;
+    double fsum = 0.0;
+    if ((s = dot_fixed(N, d_f, nullptr, part, stream, &fsum))) return s;
+    SQ_COUNT(1);
+    SQ_CUDA(sq::launch_affine(N, d_f, four_pi, -fsum / (double)N, r, sms, stream));
+    SQ_CUDA(cudaMemsetAsync(d_phi, 0, sizeof(double) * N, stream));
+    double rr = 0.0;
+    if ((s = dot_fixed(N, r, r, part, stream, &rr))) return s;
+    const double bnorm = std::sqrt(rr);
+    *iters = 0;
+    *rel_res = 0.0;
+    if (!std::isfinite(bnorm)) return fail(SQ_ERR_NOT_FINITE, "Poisson right-hand side");
+    if (bnorm == 0.0) return SQ_OK;
+    SQ_CUDA(cudaMemcpyAsync(p, r, sizeof(double) * N, cudaMemcpyDeviceToDevice, stream));
+    bool converged = false;
+    int it = 0;
+    while (it < max_iter) {
+        it++;
+        SQ_COUNT(1);
+        SQ_CUDA(sq::launch_neg_laplacian(n, w, p, Ap, sms, stream));
+        double pAp = 0.0;
+        if ((s = dot_fixed(N, p, Ap, part, stream, &pAp))) return s;
+        if (!(pAp > 0.0)) return fail(SQ_ERR_NOT_FINITE, "Poisson CG breakdown at iteration %d", it);
+        const double alpha = rr / pAp;
+        SQ_COUNT(1);
+        SQ_CUDA(sq::launch_cg_step(N, alpha, p, Ap, d_phi, r, sms, stream));
+        double rr_new = 0.0;
+        if ((s = dot_fixed(N, r, r, part, stream, &rr_new))) return s;
+        *rel_res = std::sqrt(rr_new) / bnorm;
+        if (*rel_res <= tol) {
+            converged = true;
+            break;
+        }
+        SQ_COUNT(1);
+        SQ_CUDA(sq::launch_cg_dir(N, rr_new / rr, r, p, sms, stream));
+        rr = rr_new;
+    }
+    *iters = it;
+    // rounding lets a constant creep in: restore the zero-mean gauge
+    double psum = 0.0;
+    if ((s = dot_fixed(N, d_phi, nullptr, part, stream, &psum))) return s;
+    SQ_COUNT(1);
+    SQ_CUDA(sq::launch_affine(N, d_phi, 1.0, -psum / (double)N, d_phi, sms, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    if (!converged)
+        return fail(SQ_ERR_TIMEOUT, "Poisson CG: relative residual %.3e after %d iterations", *rel_res, it);
+    return SQ_OK;
+}
+
+}  // namespace
+
+extern "C" sq_status sq_lda_pw92(long long n, const double *d_rho, double *d_exc, double *d_vxc, void *stream_)
+{
+    g_last_error[0] = 0;
+    if (n < 1 || !d_rho || !d_exc || !d_vxc) return fail(SQ_ERR_ARG, "n = %lld or a null pointer", n);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    SQ_COUNT(1);
+    SQ_CUDA(sq::launch_lda_pw92(n, d_rho, d_exc, d_vxc, current_sms(), stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_pseudocharge(const int n[3], const double box[3], int natom, const double *R, const double *Z,
+                                     double sigma_b, double *d_b, void *stream_)
+{
+    g_last_error[0] = 0;
+    sq_status s;
+    if ((s = check_grid(n, box))) return s;
+    if (!d_b || natom < 0 || (natom > 0 && (!R || !Z))) return fail(SQ_ERR_ARG, "null argument or natom = %d", natom);
+    if (!(sigma_b > 0) || !std::isfinite(sigma_b)) return fail(SQ_ERR_ARG, "sigma_b = %g", sigma_b);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    std::vector<double> rz(4 * (size_t)std::max(natom, 1), 0.0);
+    for (int J = 0; J < natom; J++) {
+        for (int a = 0; a < 3; a++) rz[4 * J + a] = R[3 * J + a];
+        rz[4 * J + 3] = Z[J];
+        for (int a = 0; a < 4; a++)
+            if (!std::isfinite(rz[4 * J + a])) return fail(SQ_ERR_NOT_FINITE, "atom %d", J);
+    }
+    DevBuf d_rz;
+    SQ_CUDA(cudaMalloc(&d_rz.p, sizeof(double) * rz.size()));
+    SQ_CUDA(cudaMemcpyAsync(d_rz.p, rz.data(), sizeof(double) * rz.size(), cudaMemcpyHostToDevice, stream));
+    const double h[3] = {box[0] / n[0], box[1] / n[1], box[2] / n[2]};
+    SQ_COUNT(1);
+    SQ_CUDA(sq::launch_pseudocharge(n, h, box, natom, d_rz.p, sigma_b, d_b, current_sms(), stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_poisson_periodic(const int n[3], const double box[3], int fd_order, const double *d_f,
+                                         double tol, int max_iter, double *d_phi, int *iters, double *rel_res,
+                                         void *stream_)
+{
+    g_last_error[0] = 0;
+    sq_status s;
+    if ((s = check_grid(n, box))) return s;
+    if (fd_order < 2 || fd_order > 2 * kMaxHalfWidth || fd_order % 2) return fail(SQ_ERR_ARG, "fd_order %d", fd_order);
+    if (!d_f || !d_phi || !iters || !rel_res) return fail(SQ_ERR_ARG, "null argument");
+    if (!(tol > 0) || max_iter < 1) return fail(SQ_ERR_ARG, "tol = %g, max_iter = %d", tol, max_iter);
+    const long long N = (long long)n[0] * n[1] * n[2];
+    DevBuf work;
+    SQ_CUDA(cudaMalloc(&work.p, sizeof(double) * (3 * (size_t)N + kDotBlocks)));
+    return poisson_cg(n, box, fd_order, d_f, tol, max_iter, d_phi, work.p, iters, rel_res, (cudaStream_t)stream_);
+}
+
+extern "C" sq_status sq_effective_potential(const int n[3], const double box[3], int fd_order, const double *d_rho,
+                                            const double *d_b, double tol, int max_iter, double *d_phi,
+                                            double *d_exc, double *d_vxc, double *d_veff, int *iters,
+                                            double *rel_res, void *stream_)
+{
+    g_last_error[0] = 0;
+    sq_status s;
+    if ((s = check_grid(n, box))) return s;
+    if (fd_order < 2 || fd_order > 2 * kMaxHalfWidth || fd_order % 2) return fail(SQ_ERR_ARG, "fd_order %d", fd_order);
+    if (!d_rho || !d_b || !d_phi || !d_exc || !d_vxc || !d_veff || !iters || !rel_res)
+        return fail(SQ_ERR_ARG, "null argument");
+    if (!(tol > 0) || max_iter < 1) return fail(SQ_ERR_ARG, "tol = %g, max_iter = %d", tol, max_iter);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const long long N = (long long)n[0] * n[1] * n[2];
+    const int sms = current_sms();
+    DevBuf work;
+    SQ_CUDA(cudaMalloc(&work.p, sizeof(double) * (4 * (size_t)N + kDotBlocks)));
+    double *f = work.p + 3 * N + kDotBlocks;
+    SQ_COUNT(1);
+    SQ_CUDA(sq::launch_add(N, d_rho, d_b, f, sms, stream));
+    if ((s = poisson_cg(n, box, fd_order, f, tol, max_iter, d_phi, work.p, iters, rel_res, stream))) return s;
+    SQ_COUNT(2);
+    SQ_CUDA(sq::launch_lda_pw92(N, d_rho, d_exc, d_vxc, sms, stream));
+    SQ_CUDA(sq::launch_add(N, d_vxc, d_phi, d_veff, sms, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    return SQ_OK;
+}

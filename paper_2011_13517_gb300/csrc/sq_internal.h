@@ -145,4 +145,25 @@ cudaError_t cluster_prepare(int nc, int amax, int fmax, int kb_fma, size_t *smem
 cudaError_t launch_cluster(const RecursionArgs<float> &args, int amax, int fmax, int nclusters, size_t smem,
                            int *err, cudaStream_t stream);
 
+// Self-consistency pieces (sq_electro.cu), FP64.  LapWeights: c[a][d] = FD weight c_d / h_a^2 of the
+// kinetic term's Laplacian along axis a, d = 0..p.
+struct LapWeights {
+    int p;
+    double c[3][kMaxHalfWidth + 1];
+};
+constexpr int kDotBlocks = 256;   // partial sums written by launch_dot_partial
+cudaError_t launch_lda_pw92(long long n, const double *rho, double *exc, double *vxc, int num_sms, cudaStream_t stream);
+// d_RZ: device [natom][4] = (x, y, z, Z)
+cudaError_t launch_pseudocharge(const int n[3], const double h[3], const double L[3], int natom, const double *d_RZ,
+                                double sigma, double *b, int num_sms, cudaStream_t stream);
+cudaError_t launch_neg_laplacian(const int n[3], const LapWeights &w, const double *v, double *out, int num_sms,
+                                 cudaStream_t stream);
+// part[kDotBlocks] = per-block sums of a.b (of a when b is null)
+cudaError_t launch_dot_partial(long long n, const double *a, const double *b, double *part, cudaStream_t stream);
+cudaError_t launch_affine(long long n, const double *in, double s, double c, double *out, int num_sms, cudaStream_t stream);
+cudaError_t launch_cg_step(long long n, double alpha, const double *p, const double *Ap, double *x, double *r,
+                           int num_sms, cudaStream_t stream);
+cudaError_t launch_cg_dir(long long n, double beta, const double *r, double *p, int num_sms, cudaStream_t stream);
+cudaError_t launch_add(long long n, const double *a, const double *b, double *out, int num_sms, cudaStream_t stream);
+
 }  // namespace sq

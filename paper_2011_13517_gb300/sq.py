@@ -34,7 +34,8 @@ EXPORTS = ["sq_build_hamiltonian", "sq_density", "sq_fermi_level", "sq_fermi_wei
            "sq_get_spectral_bounds", "sq_get_moments", "sq_copy_moments", "sq_get_cube", "sq_get_timing",
            "sq_kernel_launches", "sq_fma_throughput", "sq_mma_throughput", "sq_moments_noalloc", "sq_batch_create", "sq_batch_density",
            "sq_batch_info", "sq_batch_destroy", "sq_density_vjp", "sq_kernel_name", "sq_destroy",
-           "sq_status_string", "sq_last_error"]
+           "sq_status_string", "sq_last_error", "sq_lda_pw92", "sq_pseudocharge", "sq_poisson_periodic",
+           "sq_effective_potential"]
 
 
 class SQError(RuntimeError):
@@ -281,6 +282,55 @@ def sq_fma_throughput(precision, stream=None):
     t, ms = ctypes.c_double(), ctypes.c_double()
     _check(lib().sq_fma_throughput(int(precision), ctypes.byref(t), ctypes.byref(ms), _stream(stream)))
     return t.value, ms.value
+
+
+def _grid(n, box):
+    return (ctypes.c_int * 3)(*[int(v) for v in n]), (ctypes.c_double * 3)(*[float(v) for v in box])
+
+
+def sq_lda_pw92(d_rho, d_exc, d_vxc, stream=None):
+    """sq_lda_pw92: eps_xc and V_xc of the LDA (Slater + Perdew-Wang) at every point of d_rho."""
+    n = d_rho.numel()
+    _check(lib().sq_lda_pw92(ctypes.c_longlong(n), _dev_ptr(d_rho), _dev_ptr(d_exc, numel=n), _dev_ptr(d_vxc, numel=n),
+                             _stream(stream)))
+
+
+def sq_pseudocharge(n, box, R, Z, sigma_b, d_b, stream=None):
+    """sq_pseudocharge: Gaussian pseudocharges of the nuclei on the grid (R [natom, 3] bohr, Z [natom])."""
+    gn, gb = _grid(n, box)
+    R = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(-1, 3))
+    Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64).reshape(-1))
+    if R.shape[0] != Z.size:
+        raise ValueError("R and Z disagree on the atom count")
+    N = int(np.prod([int(v) for v in n]))
+    _check(lib().sq_pseudocharge(gn, gb, ctypes.c_int(Z.size), R.ctypes.data_as(ctypes.c_void_p),
+                                 Z.ctypes.data_as(ctypes.c_void_p), ctypes.c_double(sigma_b), _dev_ptr(d_b, numel=N),
+                                 _stream(stream)))
+
+
+def sq_poisson_periodic(n, box, fd_order, d_f, d_phi, tol=1e-11, max_iter=5000, stream=None):
+    """sq_poisson_periodic: phi of -(1/4 pi) L_h phi = f - mean f; returns (iterations, relative residual)."""
+    gn, gb = _grid(n, box)
+    N = int(np.prod([int(v) for v in n]))
+    it, res = ctypes.c_int(), ctypes.c_double()
+    _check(lib().sq_poisson_periodic(gn, gb, ctypes.c_int(fd_order), _dev_ptr(d_f, numel=N), ctypes.c_double(tol),
+                                     ctypes.c_int(max_iter), _dev_ptr(d_phi, numel=N), ctypes.byref(it),
+                                     ctypes.byref(res), _stream(stream)))
+    return it.value, res.value
+
+
+def sq_effective_potential(n, box, fd_order, d_rho, d_b, d_phi, d_exc, d_vxc, d_veff, tol=1e-11, max_iter=5000,
+                           stream=None):
+    """sq_effective_potential: phi(rho + b), eps_xc, V_xc and V_eff = V_xc + phi; returns (iterations, residual)."""
+    gn, gb = _grid(n, box)
+    N = int(np.prod([int(v) for v in n]))
+    it, res = ctypes.c_int(), ctypes.c_double()
+    _check(lib().sq_effective_potential(gn, gb, ctypes.c_int(fd_order), _dev_ptr(d_rho, numel=N),
+                                        _dev_ptr(d_b, numel=N), ctypes.c_double(tol), ctypes.c_int(max_iter),
+                                        _dev_ptr(d_phi, numel=N), _dev_ptr(d_exc, numel=N), _dev_ptr(d_vxc, numel=N),
+                                        _dev_ptr(d_veff, numel=N), ctypes.byref(it), ctypes.byref(res),
+                                        _stream(stream)))
+    return it.value, res.value
 
 
 def sq_energy(h: Handle, stream=None):

@@ -118,3 +118,23 @@ def test_host_gauss_rule_cuts_at_an_exhausted_krylov_space():
     assert abs(w.sum() - 1.0) < 1e-14 and w[2] == 0.0 and w[3] == 0.0
     lam = np.linalg.eigvalsh(np.array([[0.1, 0.5], [0.5, -0.2]]))
     np.testing.assert_allclose(np.sort(nodes[:2]), lam, rtol=0, atol=1e-14)
+
+
+def test_scf_entry_points_reject_bad_arguments_before_any_launch():
+    """sq_lda_pw92, sq_pseudocharge, sq_poisson_periodic and sq_effective_potential check their
+    arguments on the host (no device work, so this runs without a GPU)."""
+    import ctypes
+    L = sq.lib()
+    n = (ctypes.c_int * 3)(8, 8, 8)
+    box = (ctypes.c_double * 3)(4.0, 4.0, 4.0)
+    null = ctypes.c_void_p(0)
+    it, res = ctypes.c_int(), ctypes.c_double()
+    assert L.sq_lda_pw92(ctypes.c_longlong(0), null, null, null, null) == 1
+    bad_n = (ctypes.c_int * 3)(8, 0, 8)
+    assert L.sq_pseudocharge(bad_n, box, 0, null, null, ctypes.c_double(1.0), null, null) == 1
+    assert L.sq_pseudocharge(n, box, 0, null, null, ctypes.c_double(-1.0), ctypes.c_void_p(8), null) == 1
+    for order, tol, iters in ((3, 1e-10, 10), (18, 1e-10, 10), (12, 0.0, 10), (12, 1e-10, 0)):
+        assert L.sq_poisson_periodic(n, box, order, ctypes.c_void_p(8), ctypes.c_double(tol), iters,
+                                     ctypes.c_void_p(8), ctypes.byref(it), ctypes.byref(res), null) == 1
+    assert L.sq_effective_potential(n, box, 12, null, null, ctypes.c_double(1e-10), 10, null, null, null, null,
+                                    ctypes.byref(it), ctypes.byref(res), null) == 1
