@@ -457,6 +457,26 @@ sq_status sq_effective_potential(const int n[3], const double box[3], int fd_ord
                                  const double *d_b, double tol, int max_iter, double *d_phi, double *d_exc,
                                  double *d_vxc, double *d_veff, int *iters, double *rel_res, void *stream);
 
+/*
+ * Anderson mixing of the effective potential between SCF iterations (Sec. 3: the SCF iteration mixes
+ * V_eff and stops on the normalised error of V_eff).  A mixer holds, on the device, the previous
+ * input potential and residual and the differences of the last `history` steps.
+ *
+ * sq_mixer_create -- n grid points, history 0..32 (0: linear mixing), 0 < beta <= 1.  Allocates
+ *   (3 + 2 history) n + 256 doubles.  Errors: SQ_ERR_ARG, SQ_ERR_OOM.
+ * sq_mixer_step -- with F = V_out - V_in: rel_err = |F| / |V_out|; gamma minimises
+ *   |F - sum_j gamma_j dF_j| over the held differences (dV_j, dF_j) of V_in and F (normal equations,
+ *   regularised by 1e-12 of their mean diagonal); V_next = V_in + beta F - sum_j gamma_j (dV_j + beta dF_j).
+ *   d_vin, d_vout: device [n] inputs; d_vnext: device [n] output (may be d_vin).  Synchronises
+ *   `stream`.  Errors: SQ_ERR_ARG, SQ_ERR_NOT_FINITE, SQ_ERR_CUDA.
+ * sq_mixer_destroy -- release (NULL is ignored).
+ */
+typedef struct sq_mixer_s *sq_mixer;
+sq_status sq_mixer_create(long long n, int history, double beta, sq_mixer *out);
+sq_status sq_mixer_step(sq_mixer m, const double *d_vin, const double *d_vout, double *d_vnext, double *rel_err,
+                        void *stream);
+void sq_mixer_destroy(sq_mixer m);
+
 /* Release a handle and its device workspace (NULL is ignored).  Synchronises the device. */
 void sq_destroy(sq_handle h);
 

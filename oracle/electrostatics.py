@@ -152,3 +152,47 @@ def effective_potential(rho, cell, sigma_b):
     phi = poisson_periodic(np.asarray(rho) + b, cell)
     _, vxc = lda_pw92(rho)
     return vxc + phi, phi, vxc, b
+
+
+def anderson_next(v_in, v_out, hist, beta, m):
+    """One Anderson mixing step of the effective potential (Sec. 3, SCF mixing).  F = V_out - V_in; the
+    history `hist` holds the previous (V_in, F) and the differences (dV_j, dF_j) of the last m steps;
+    gamma minimises |F - sum_j gamma_j dF_j| and V_next = V_in + beta F - sum_j gamma_j (dV_j + beta dF_j).
+    Returns (V_next, |F| / |V_out|)."""
+    F = v_out - v_in
+    if hist.get("prev") is not None:
+        pv, pF = hist["prev"]
+        hist.setdefault("d", []).append((v_in - pv, F - pF))
+        hist["d"] = hist["d"][-m:] if m > 0 else []
+    hist["prev"] = (v_in.copy(), F.copy())
+    nxt = v_in + beta * F
+    d = hist.get("d", [])
+    if d:
+        dF = np.array([x[1] for x in d])
+        dV = np.array([x[0] for x in d])
+        G = dF @ dF.T
+        G = G + 1e-12 * np.trace(G) / len(d) * np.eye(len(d))
+        gam = np.linalg.solve(G, dF @ F)
+        nxt = nxt - gam @ (dV + beta * dF)
+    return nxt, float(np.linalg.norm(F) / np.linalg.norm(v_out))
+
+
+def scf(cell, sigma_b, beta=0.3, m=5, tol=1e-9, max_iter=100, K=None, v0=None):
+    """Self-consistent field of the SQ density (Sec. 3 flow): V_in -> rho (Clenshaw-Curtis SQ with the
+    library-independent oracle, spectral bounds of V_in) -> V_out = V_xc(rho) + phi(rho + b) -> Anderson
+    mixing, until |V_out - V_in| / |V_out| <= tol.  Returns the last V_in, rho, lambda_f, iterations and
+    the error history."""
+    import copy
+    c = copy.deepcopy(cell)
+    v = np.asarray(cell.veff if v0 is None else v0, dtype=np.float64).reshape(-1).copy()
+    hist, errs = {}, []
+    for it in range(1, max_iter + 1):
+        c.veff = v.reshape(cell.veff.shape)
+        r = oracle.sq_solve(c, force=False, K=K)
+        vout, _, _, _ = effective_potential(r["rho"], c, sigma_b)
+        v_next, err = anderson_next(v, vout, hist, beta, m)
+        errs.append(err)
+        if err <= tol:
+            return dict(veff=v, rho=r["rho"], lam_f=r["lam_f"], iters=it, errors=errs)
+        v = v_next
+    return dict(veff=v, rho=r["rho"], lam_f=r["lam_f"], iters=max_iter, errors=errs)

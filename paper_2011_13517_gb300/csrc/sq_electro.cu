@@ -5,7 +5,8 @@
 //   k_pseudocharge    b(x) = sum_J -Z_J (2 pi s^2)^(-3/2) exp(-|x - R_J|^2 / (2 s^2)), minimum image;
 //   k_neg_laplacian   -L_h v for the periodic finite-difference Laplacian of the kinetic term;
 //   k_dot_partial     fixed-order per-block partial sums of a.b (the host adds the blocks in order);
-//   k_cg_*            vector updates of the conjugate-gradient solve of -(1/4 pi) L_h phi = f (Eq. Poisson).
+//   k_cg_*            vector updates of the conjugate-gradient solve of -(1/4 pi) L_h phi = f (Eq. Poisson);
+//   k_lincomb         alpha a + beta b, the vector steps of the Anderson mixing of V_eff (Sec. 3).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -130,6 +131,13 @@ __global__ void k_add(long long n, const double *a, const double *b, double *out
         out[i] = a[i] + b[i];
 }
 
+// out = alpha a + beta b (out may be a or b)
+__global__ void k_lincomb(long long n, double alpha, const double *a, double beta, const double *b, double *out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = alpha * a[i] + beta * b[i];
+}
+
 int grid_of(long long n, int num_sms)
 {
     long long g = (n + kEBlock - 1) / kEBlock;
@@ -185,6 +193,13 @@ cudaError_t launch_cg_step(long long n, double alpha, const double *p, const dou
 cudaError_t launch_cg_dir(long long n, double beta, const double *r, double *p, int num_sms, cudaStream_t stream)
 {
     k_cg_dir<<<grid_of(n, num_sms), kEBlock, 0, stream>>>(n, beta, r, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lincomb(long long n, double alpha, const double *a, double beta, const double *b, double *out,
+                           int num_sms, cudaStream_t stream)
+{
+    k_lincomb<<<grid_of(n, num_sms), kEBlock, 0, stream>>>(n, alpha, a, beta, b, out);
     return cudaGetLastError();
 }
 

@@ -2711,3 +2711,126 @@ extern "C" sq_status sq_effective_potential(const int n[3], const double box[3],
     SQ_CUDA(cudaStreamSynchronize(stream));
     return SQ_OK;
 }
+
+// ------------------------------------------------------------------------------------------------
+// Anderson mixing of the effective potential (Sec. 3: "In every SCF iteration, we mix the effective
+// potential V_eff"): vectors stay on the device, the small least-squares system is solved on the host.
+
+struct sq_mixer_s {
+    long long n = 0;
+    int m = 0;            // history length
+    double beta = 0.0;    // mixing parameter
+    int count = 0;        // differences held (<= m)
+    int head = 0;         // slot of the next difference
+    bool has_prev = false;
+    double *buf = nullptr;   // [prev_v, prev_F, F, dV[m], dF[m], part]
+    double *prev_v() const { return buf; }
+    double *prev_F() const { return buf + n; }
+    double *F() const { return buf + 2 * n; }
+    double *dV(int j) const { return buf + (3 + (size_t)j) * n; }
+    double *dF(int j) const { return buf + (3 + (size_t)m + j) * n; }
+    double *part() const { return buf + (3 + 2 * (size_t)m) * n; }
+};
+
+extern "C" sq_status sq_mixer_create(long long n, int history, double beta, sq_mixer *out)
+{
+    g_last_error[0] = 0;
+    if (!out || n < 1 || history < 0 || history > 32 || !(beta > 0) || !(beta <= 1))
+        return fail(SQ_ERR_ARG, "n = %lld, history = %d, beta = %g", n, history, beta);
+    *out = nullptr;
+    sq_mixer_s *m = new sq_mixer_s();
+    m->n = n;
+    m->m = history;
+    m->beta = beta;
+    const size_t doubles = (3 + 2 * (size_t)history) * (size_t)n + kDotBlocks;
+    if (cudaMalloc(&m->buf, sizeof(double) * doubles) != cudaSuccess) {
+        delete m;
+        cudaGetLastError();
+        return fail(SQ_ERR_OOM, "mixer: %zu doubles", doubles);
+    }
+    *out = m;
+    return SQ_OK;
+}
+
+extern "C" void sq_mixer_destroy(sq_mixer m)
+{
+    if (!m) return;
+    if (m->buf) cudaFree(m->buf);
+    delete m;
+}
+
+extern "C" sq_status sq_mixer_step(sq_mixer m, const double *d_vin, const double *d_vout, double *d_vnext,
+                                   double *rel_err, void *stream_)
+{
+    g_last_error[0] = 0;
+    if (!m || !d_vin || !d_vout || !d_vnext || !rel_err) return fail(SQ_ERR_ARG, "null argument");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const long long n = m->n;
+    const int sms = current_sms();
+    sq_status s;
+    // F = V_out - V_in and its size relative to V_out
+    SQ_COUNT(1);
+    SQ_CUDA(sq::launch_lincomb(n, 1.0, d_vout, -1.0, d_vin, m->F(), sms, stream));
+    double ff = 0.0, oo = 0.0;
+    if ((s = dot_fixed(n, m->F(), m->F(), m->part(), stream, &ff))) return s;
+    if ((s = dot_fixed(n, d_vout, d_vout, m->part(), stream, &oo))) return s;
+    if (!std::isfinite(ff) || !std::isfinite(oo)) return fail(SQ_ERR_NOT_FINITE, "mixer input");
+    *rel_err = oo > 0.0 ? std::sqrt(ff / oo) : std::sqrt(ff);
+    // the newest differences (dV, dF) = (V_in - V_in,prev, F - F_prev)
+    if (m->has_prev && m->m > 0) {
+        const int j = m->head;
+        SQ_COUNT(2);
+        SQ_CUDA(sq::launch_lincomb(n, 1.0, d_vin, -1.0, m->prev_v(), m->dV(j), sms, stream));
+        SQ_CUDA(sq::launch_lincomb(n, 1.0, m->F(), -1.0, m->prev_F(), m->dF(j), sms, stream));
+        m->head = (m->head + 1) % m->m;
+        if (m->count < m->m) m->count++;
+    }
+    SQ_CUDA(cudaMemcpyAsync(m->prev_v(), d_vin, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream));
+    SQ_CUDA(cudaMemcpyAsync(m->prev_F(), m->F(), sizeof(double) * n, cudaMemcpyDeviceToDevice, stream));
+    m->has_prev = true;
+    // V_next = V_in + beta F - sum_j gamma_j (dV_j + beta dF_j), gamma minimising |F - sum_j gamma_j dF_j|
+    SQ_COUNT(1);
+    SQ_CUDA(sq::launch_lincomb(n, 1.0, d_vin, m->beta, m->F(), d_vnext, sms, stream));
+    const int k = m->count;
+    if (k > 0) {
+        double G[32 * 32], rhs[32], gam[32];
+        for (int a = 0; a < k; a++) {
+            for (int b = a; b < k; b++) {
+                if ((s = dot_fixed(n, m->dF(a), m->dF(b), m->part(), stream, &G[a * k + b]))) return s;
+                G[b * k + a] = G[a * k + b];
+            }
+            if ((s = dot_fixed(n, m->dF(a), m->F(), m->part(), stream, &rhs[a]))) return s;
+        }
+        double tr = 0.0;
+        for (int a = 0; a < k; a++) tr += G[a * k + a];
+        for (int a = 0; a < k; a++) G[a * k + a] += 1e-12 * tr / k;
+        // Gaussian elimination with partial pivoting (k <= 32)
+        for (int c = 0; c < k; c++) {
+            int piv = c;
+            for (int r = c + 1; r < k; r++)
+                if (std::fabs(G[r * k + c]) > std::fabs(G[piv * k + c])) piv = r;
+            if (!(std::fabs(G[piv * k + c]) > 0.0)) return fail(SQ_ERR_NOT_FINITE, "mixer: singular history");
+            if (piv != c) {
+                for (int q = 0; q < k; q++) std::swap(G[c * k + q], G[piv * k + q]);
+                std::swap(rhs[c], rhs[piv]);
+            }
+            for (int r = c + 1; r < k; r++) {
+                const double f = G[r * k + c] / G[c * k + c];
+                for (int q = c; q < k; q++) G[r * k + q] -= f * G[c * k + q];
+                rhs[r] -= f * rhs[c];
+            }
+        }
+        for (int c = k - 1; c >= 0; c--) {
+            double t = rhs[c];
+            for (int q = c + 1; q < k; q++) t -= G[c * k + q] * gam[q];
+            gam[c] = t / G[c * k + c];
+        }
+        for (int a = 0; a < k; a++) {
+            SQ_COUNT(2);
+            SQ_CUDA(sq::launch_lincomb(n, 1.0, d_vnext, -gam[a], m->dV(a), d_vnext, sms, stream));
+            SQ_CUDA(sq::launch_lincomb(n, 1.0, d_vnext, -gam[a] * m->beta, m->dF(a), d_vnext, sms, stream));
+        }
+    }
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    return SQ_OK;
+}

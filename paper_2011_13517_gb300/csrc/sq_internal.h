@@ -165,5 +165,7 @@ cudaError_t launch_cg_step(long long n, double alpha, const double *p, const dou
                            int num_sms, cudaStream_t stream);
 cudaError_t launch_cg_dir(long long n, double beta, const double *r, double *p, int num_sms, cudaStream_t stream);
 cudaError_t launch_add(long long n, const double *a, const double *b, double *out, int num_sms, cudaStream_t stream);
+cudaError_t launch_lincomb(long long n, double alpha, const double *a, double beta, const double *b, double *out,
+                           int num_sms, cudaStream_t stream);
 
 }  // namespace sq

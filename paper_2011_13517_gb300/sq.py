@@ -35,7 +35,7 @@ EXPORTS = ["sq_build_hamiltonian", "sq_density", "sq_fermi_level", "sq_fermi_wei
            "sq_kernel_launches", "sq_fma_throughput", "sq_mma_throughput", "sq_moments_noalloc", "sq_batch_create", "sq_batch_density",
            "sq_batch_info", "sq_batch_destroy", "sq_density_vjp", "sq_kernel_name", "sq_destroy",
            "sq_status_string", "sq_last_error", "sq_lda_pw92", "sq_pseudocharge", "sq_poisson_periodic",
-           "sq_effective_potential"]
+           "sq_effective_potential", "sq_mixer_create", "sq_mixer_step", "sq_mixer_destroy"]
 
 
 class SQError(RuntimeError):
@@ -100,12 +100,14 @@ def lib():
         L.sq_batch_destroy.restype = None
         L.sq_destroy.argtypes = [vp]
         L.sq_destroy.restype = None
+        L.sq_mixer_destroy.restype = None
+        L.sq_mixer_destroy.argtypes = [vp]
         L.sq_status_string.argtypes = [ctypes.c_int]
         L.sq_status_string.restype = ctypes.c_char_p
         L.sq_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name not in ("sq_destroy", "sq_status_string", "sq_last_error", "sq_kernel_launches", "sq_batch_destroy",
-                            "sq_kernel_name"):
+                            "sq_kernel_name", "sq_mixer_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         L.sq_kernel_launches.restype = ctypes.c_longlong
         _lib = L
@@ -331,6 +333,44 @@ def sq_effective_potential(n, box, fd_order, d_rho, d_b, d_phi, d_exc, d_vxc, d_
                                         _dev_ptr(d_veff, numel=N), ctypes.byref(it), ctypes.byref(res),
                                         _stream(stream)))
     return it.value, res.value
+
+
+class Mixer:
+    """Owns an sq_mixer (Anderson mixing of V_eff over SCF iterations)."""
+
+    def __init__(self, ptr, n):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.n = n
+
+    def close(self):
+        if self.ptr:
+            lib().sq_mixer_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sq_mixer_create(n, history=5, beta=0.3):
+    out = ctypes.c_void_p()
+    _check(lib().sq_mixer_create(ctypes.c_longlong(int(n)), ctypes.c_int(history), ctypes.c_double(beta),
+                                 ctypes.byref(out)))
+    return Mixer(out.value, int(n))
+
+
+def sq_mixer_step(m: Mixer, d_vin, d_vout, d_vnext, stream=None):
+    """One Anderson step: writes V_next, returns |V_out - V_in| / |V_out|."""
+    err = ctypes.c_double()
+    _check(lib().sq_mixer_step(m.ptr, _dev_ptr(d_vin, numel=m.n), _dev_ptr(d_vout, numel=m.n),
+                               _dev_ptr(d_vnext, numel=m.n), ctypes.byref(err), _stream(stream)))
+    return err.value
+
+
+def sq_mixer_destroy(m: Mixer):
+    m.close()
 
 
 def sq_energy(h: Handle, stream=None):

@@ -102,3 +102,42 @@ def test_poisson_reports_non_convergence():
     with pytest.raises(sq.SQError) as ei:
         sq.sq_poisson_periodic(c.n, c.box, c.fd_order, dev(f), phi, tol=1e-14, max_iter=2)
     assert ei.value.status == 6
+
+
+def test_scf_tiny_cell_matches_oracle():
+    """The SCF loop on the GPU (sq_build_hamiltonian of V_in with the library's spectral bounds,
+    sq_density FP64, sq_effective_potential, sq_mixer_step) against the oracle's SCF with the same
+    Anderson mixing (beta 0.3, history 5) to |V_out - V_in| / |V_out| <= 1e-10: the same number of
+    iterations, and V_eff, rho and lambda_f at the fixed point within 1e-8 (relative to their largest
+    values; both iterate the same map, so they differ by rounding amplified over the iterations)."""
+    c = cells.tiny_cell()
+    ref = es.scf(c, SIGMA_B, beta=0.3, m=5, tol=1e-10, max_iter=80)
+    Z = es.valence_charges(c)
+    N = c.N_d
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    sq.sq_pseudocharge(c.n, c.box, c.R, Z, SIGMA_B, b)
+    v_in = dev(c.veff.reshape(-1))
+    rho = torch.empty(N, dtype=torch.float64, device="cuda")
+    phi, exc, vxc, v_out = [torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(4)]
+    mixer = sq.sq_mixer_create(N, history=5, beta=0.3)
+    errs, lam = [], None
+    try:
+        for it in range(1, 81):
+            h = sq.build_for_cell(c, d_veff=v_in)
+            lam = sq.sq_density(h, c.K, c.kT, c.N_e, sq.SQ_FP64, 0, rho)
+            h.close()
+            sq.sq_effective_potential(c.n, c.box, c.fd_order, rho, b, phi, exc, vxc, v_out, tol=1e-13)
+            rho_it = rho.cpu().numpy()
+            v_it = v_in.cpu().numpy()
+            err = sq.sq_mixer_step(mixer, v_in, v_out, v_in)
+            errs.append(err)
+            if err <= 1e-10:
+                break
+    finally:
+        mixer.close()
+    print("GPU SCF errors", ["%.1e" % e for e in errs])
+    print("oracle SCF errors", ["%.1e" % e for e in ref["errors"]])
+    assert errs[-1] <= 1e-10 and abs(len(errs) - ref["iters"]) <= 1
+    np.testing.assert_allclose(v_it, ref["veff"], rtol=0, atol=1e-8 * np.abs(ref["veff"]).max())
+    np.testing.assert_allclose(rho_it, ref["rho"], rtol=0, atol=1e-8 * np.abs(ref["rho"]).max())
+    assert abs(lam - ref["lam_f"]) < 1e-8

@@ -99,3 +99,45 @@ def test_pseudocharge_normalisation_and_self_energy():
     e_disc = -0.5 * dV * float(np.sum(bJ * VJ))
     e_cont = es.self_energy_continuum([Z[J]], sig)
     assert abs(e_disc - e_cont) < 1e-6 * abs(e_cont), (e_disc, e_cont)
+
+
+def test_anderson_without_history_is_linear_mixing():
+    rng = np.random.default_rng(4)
+    hist = {}
+    v0, o0 = rng.standard_normal(50), rng.standard_normal(50)
+    v1, _ = es.anderson_next(v0, o0, hist, 0.3, 0)
+    np.testing.assert_allclose(v1, v0 + 0.3 * (o0 - v0), rtol=0, atol=1e-15)
+    o1 = rng.standard_normal(50)
+    v2, _ = es.anderson_next(v1, o1, hist, 0.3, 0)
+    np.testing.assert_allclose(v2, v1 + 0.3 * (o1 - v1), rtol=0, atol=1e-15)
+
+
+def test_anderson_finds_the_fixed_point_of_an_affine_map():
+    # V_out = A V + c with a contraction A: the fixed point solves (I - A) V = c; Anderson mixing with
+    # enough history reaches it in far fewer steps than linear mixing
+    rng = np.random.default_rng(8)
+    n = 40
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(rng.uniform(-0.9, 0.9, n)) @ Q.T
+    c = rng.standard_normal(n)
+    exact = np.linalg.solve(np.eye(n) - A, c)
+    v, hist = np.zeros(n), {}
+    for it in range(200):
+        v_next, err = es.anderson_next(v, A @ v + c, hist, 0.5, 10)
+        if err < 1e-12:
+            break
+        v = v_next
+    assert it < 60
+    np.testing.assert_allclose(v, exact, rtol=0, atol=1e-10 * np.abs(exact).max())
+
+
+def test_scf_fixed_point_is_self_consistent_and_independent_of_the_mixing():
+    c = cells.tiny_cell()
+    r1 = es.scf(c, 1.0, beta=0.3, m=5, tol=1e-10, max_iter=80)
+    r2 = es.scf(c, 1.0, beta=0.5, m=3, tol=1e-10, max_iter=80)
+    assert r1["iters"] < 80 and r2["iters"] < 80
+    scale = np.abs(r1["veff"]).max()
+    assert np.max(np.abs(r1["veff"] - r2["veff"])) < 1e-8 * scale
+    vout, _, _, _ = es.effective_potential(r1["rho"], c, 1.0)
+    assert np.linalg.norm(vout - r1["veff"]) <= 1e-10 * np.linalg.norm(vout)
+    assert abs(r1["rho"].sum() * float(np.prod(c.h)) - c.N_e) < 1e-9 * c.N_e
