@@ -477,6 +477,29 @@ sq_status sq_mixer_step(sq_mixer m, const double *d_vin, const double *d_vout, d
                         void *stream);
 void sq_mixer_destroy(sq_mixer m);
 
+/*
+ * Discrete free energy and local force (Sec. 3 "Free energy", "Atomic forces"), FP64 on the grid of
+ * the self-consistency calls above; host outputs; each call synchronises `stream`.
+ *
+ * sq_self_energy -- E_self^h = -(1/2) h1 h2 h3 sum_q sum_I b_I^q V_I^q (Eq. DiscreteSelfEnergy) for the
+ *   Gaussian pseudocharges of sq_pseudocharge, V_I = -Z_I erf(r / (sqrt(2) sigma_b)) / r their
+ *   free-space potentials (minimum image).  Errors: SQ_ERR_ARG, SQ_ERR_NOT_FINITE, SQ_ERR_OOM, SQ_ERR_CUDA.
+ * sq_free_energy -- F^h = F_band + h1 h2 h3 sum_q [(eps_xc - V_xc) rho + (1/2)(b - rho) phi] + E_self
+ *   (Eq. DiscreteEnergy), with F_band = U - kT S of sq_energy (its sum over q of u^q - 2 theta s^q),
+ *   phi, eps_xc, V_xc of rho from sq_effective_potential and E_self from sq_self_energy.
+ *   Errors: SQ_ERR_ARG, SQ_ERR_NOT_FINITE, SQ_ERR_OOM, SQ_ERR_CUDA.
+ * sq_local_force -- f_J = h1 h2 h3 sum_q (nabla_h b_J)^q phi^q (Eq. DiscreteLocalForce), nabla_h the
+ *   central first difference of order fd_order, evaluated as -h1 h2 h3 sum_q b_J^q (nabla_h phi)^q
+ *   (the same sum on the periodic grid).  force: host [natom][3] output (Ha/bohr).  Errors as above.
+ */
+sq_status sq_self_energy(const int n[3], const double box[3], int natom, const double *R, const double *Z,
+                         double sigma_b, double *E_self, void *stream);
+sq_status sq_free_energy(const int n[3], const double box[3], const double *d_rho, const double *d_b,
+                         const double *d_phi, const double *d_exc, const double *d_vxc, double F_band, double E_self,
+                         double *F, void *stream);
+sq_status sq_local_force(const int n[3], const double box[3], int fd_order, int natom, const double *R, const double *Z,
+                         double sigma_b, const double *d_phi, double *force, void *stream);
+
 /* Release a handle and its device workspace (NULL is ignored).  Synchronises the device. */
 void sq_destroy(sq_handle h);
 

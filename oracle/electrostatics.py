@@ -177,9 +177,9 @@ def anderson_next(v_in, v_out, hist, beta, m):
     return nxt, float(np.linalg.norm(F) / np.linalg.norm(v_out))
 
 
-def scf(cell, sigma_b, beta=0.3, m=5, tol=1e-9, max_iter=100, K=None, v0=None):
+def scf(cell, sigma_b, beta=0.3, m=5, tol=1e-9, max_iter=100, K=None, v0=None, bounds=None):
     """Self-consistent field of the SQ density (Sec. 3 flow): V_in -> rho (Clenshaw-Curtis SQ with the
-    library-independent oracle, spectral bounds of V_in) -> V_out = V_xc(rho) + phi(rho + b) -> Anderson
+    library-independent oracle, spectral bounds of V_in unless given) -> V_out = V_xc(rho) + phi(rho + b) -> Anderson
     mixing, until |V_out - V_in| / |V_out| <= tol.  Returns the last V_in, rho, lambda_f, iterations and
     the error history."""
     import copy
@@ -188,7 +188,7 @@ def scf(cell, sigma_b, beta=0.3, m=5, tol=1e-9, max_iter=100, K=None, v0=None):
     hist, errs = {}, []
     for it in range(1, max_iter + 1):
         c.veff = v.reshape(cell.veff.shape)
-        r = oracle.sq_solve(c, force=False, K=K)
+        r = oracle.sq_solve(c, force=False, K=K, bounds=bounds)
         vout, _, _, _ = effective_potential(r["rho"], c, sigma_b)
         v_next, err = anderson_next(v, vout, hist, beta, m)
         errs.append(err)
@@ -196,3 +196,81 @@ def scf(cell, sigma_b, beta=0.3, m=5, tol=1e-9, max_iter=100, K=None, v0=None):
             return dict(veff=v, rho=r["rho"], lam_f=r["lam_f"], iters=it, errors=errs)
         v = v_next
     return dict(veff=v, rho=r["rho"], lam_f=r["lam_f"], iters=max_iter, errors=errs)
+
+
+# ------------------------------------------------------------------------------------------------
+# Discrete free energy and local force (Sec. 3 "Free energy", "Atomic forces")
+
+def grad_h(phi, cell):
+    """The FD gradient nabla_h of the same order as the Laplacian, periodic: three arrays like phi."""
+    a = oracle.fd1_coeffs(cell.fd_order)
+    out = []
+    for ax, npax in ((0, 2), (1, 1), (2, 0)):
+        g = np.zeros_like(phi)
+        for j in range(1, a.size):
+            g += a[j] * (np.roll(phi, -j, axis=npax) - np.roll(phi, j, axis=npax))
+        out.append(g / cell.h[ax])
+    return out
+
+
+def _min_image_r2(cell, J):
+    n = [int(v) for v in cell.n]
+    d2 = 0.0
+    for a, npax in ((0, 2), (1, 1), (2, 0)):
+        t = np.arange(n[a]) * cell.h[a] - cell.R[J, a]
+        t = t - cell.box[a] * np.round(t / cell.box[a])
+        shp = [1, 1, 1]
+        shp[npax] = n[a]
+        d2 = d2 + (t * t).reshape(shp)
+    return d2
+
+
+def pseudocharge_one(cell, sigma_b, J, Z):
+    """b_J on the grid, [n3, n2, n1]."""
+    norm = (2.0 * math.pi * sigma_b * sigma_b) ** -1.5
+    return -Z * norm * np.exp(-_min_image_r2(cell, J) / (2.0 * sigma_b * sigma_b))
+
+
+def self_energy_discrete(cell, sigma_b, Z=None):
+    """E_self^h = -(1/2) h1 h2 h3 sum_q sum_I b_I^q V_I^q (Eq. DiscreteSelfEnergy), V_I the free-space
+    potential of the Gaussian b_I: -Z_I erf(r / (sqrt 2 sigma_b)) / r (minimum image)."""
+    from scipy.special import erf
+    Z = valence_charges(cell) if Z is None else np.asarray(Z, dtype=np.float64)
+    dV = float(np.prod(cell.h))
+    e = 0.0
+    for J in range(cell.natom):
+        r = np.sqrt(_min_image_r2(cell, J))
+        safe = np.where(r > 0, r, 1.0)
+        V = -Z[J] * np.where(r > 0, erf(r / (math.sqrt(2.0) * sigma_b)) / safe, math.sqrt(2.0 / math.pi) / sigma_b)
+        e += float(np.sum(pseudocharge_one(cell, sigma_b, J, Z[J]) * V))
+    return -0.5 * dV * e
+
+
+def free_energy(cell, sigma_b, rho, U, S, kT):
+    """Discrete free energy (Eq. DiscreteEnergy) at the density rho whose band energy and entropy are
+    U = sum_q u^q and S (k_B units, F_band = U - kT S):
+    F^h = U - kT S + h1 h2 h3 sum_q [(eps_xc - V_xc) rho + (1/2)(b - rho) phi] + E_self^h,
+    with phi of rho + b (zero mean) and eps_xc, V_xc of rho.  Returns (F, E_self)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    b = pseudocharge(cell, sigma_b)
+    phi = poisson_periodic(rho + b, cell)
+    exc, vxc = lda_pw92(rho)
+    dV = float(np.prod(cell.h))
+    es_ = self_energy_discrete(cell, sigma_b)
+    F = U - kT * S + dV * float(np.sum((exc - vxc) * rho + 0.5 * (b - rho) * phi)) + es_
+    return F, es_
+
+
+def local_force(cell, sigma_b, phi, Z=None):
+    """f_J = h1 h2 h3 sum_q (nabla_h b_J)^q phi^q (Eq. DiscreteLocalForce), [natom, 3]: the gradient of
+    each b_J on the grid, as printed."""
+    Z = valence_charges(cell) if Z is None else np.asarray(Z, dtype=np.float64)
+    shape = (int(cell.n[2]), int(cell.n[1]), int(cell.n[0]))
+    ph = np.asarray(phi, dtype=np.float64).reshape(shape)
+    dV = float(np.prod(cell.h))
+    f = np.zeros((cell.natom, 3))
+    for J in range(cell.natom):
+        g = grad_h(pseudocharge_one(cell, sigma_b, J, Z[J]), cell)
+        for d in range(3):
+            f[J, d] = dV * float(np.sum(g[d] * ph))
+    return f

@@ -6,7 +6,10 @@
 //   k_neg_laplacian   -L_h v for the periodic finite-difference Laplacian of the kinetic term;
 //   k_dot_partial     fixed-order per-block partial sums of a.b (the host adds the blocks in order);
 //   k_cg_*            vector updates of the conjugate-gradient solve of -(1/4 pi) L_h phi = f (Eq. Poisson);
-//   k_lincomb         alpha a + beta b, the vector steps of the Anderson mixing of V_eff (Sec. 3).
+//   k_lincomb         alpha a + beta b, the vector steps of the Anderson mixing of V_eff (Sec. 3);
+//   k_grad_h, k_local_force, k_self_energy_partial, k_free_energy_partial
+//                     the discrete local force (Eq. DiscreteLocalForce), self energy (Eq.
+//                     DiscreteSelfEnergy) and the density terms of the free energy (Eq. DiscreteEnergy).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -138,6 +141,117 @@ __global__ void k_lincomb(long long n, double alpha, const double *a, double bet
         out[i] = alpha * a[i] + beta * b[i];
 }
 
+// gradient nabla_h of the order of the Laplacian, periodic: g_a = sum_j a_j (v(x + j e_a) - v(x - j e_a)) / h_a
+__global__ void k_grad_h(int n0, int n1, int n2, GradWeights gw, const double *v, double *gx, double *gy, double *gz)
+{
+    const long long N = (long long)n0 * n1 * n2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % n0), j = (int)((q / n0) % n1), k = (int)(q / ((long long)n0 * n1));
+        const long long row = q - i, plane = (long long)k * n0 * n1;
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int d = 1; d <= gw.p; d++) {
+            const int ip = (i + d) % n0, im = ((i - d) % n0 + n0) % n0;
+            const int jp = (j + d) % n1, jm = ((j - d) % n1 + n1) % n1;
+            const int kp = (k + d) % n2, km = ((k - d) % n2 + n2) % n2;
+            sx += gw.a[0][d] * (v[row + ip] - v[row + im]);
+            sy += gw.a[1][d] * (v[plane + (long long)jp * n0 + i] - v[plane + (long long)jm * n0 + i]);
+            sz += gw.a[2][d] * (v[(long long)kp * n0 * n1 + (long long)j * n0 + i] - v[(long long)km * n0 * n1 + (long long)j * n0 + i]);
+        }
+        gx[q] = sx;
+        gy[q] = sy;
+        gz[q] = sz;
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kEBlock / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// squared minimum-image distance from grid point (i, j, k) to atom J
+__device__ __forceinline__ double min_image_r2(int i, int j, int k, double h0, double h1, double h2, double L0, double L1,
+                                               double L2, const double *RZ, int J)
+{
+    double dx = i * h0 - RZ[4 * J], dy = j * h1 - RZ[4 * J + 1], dz = k * h2 - RZ[4 * J + 2];
+    dx -= L0 * rint(dx / L0);
+    dy -= L1 * rint(dy / L1);
+    dz -= L2 * rint(dz / L2);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// per-block sums of sum_I b_I V_I over the grid points, V_I = -Z_I erf(r / (sqrt 2 s)) / r
+__global__ void k_self_energy_partial(int n0, int n1, int n2, double h0, double h1, double h2, double L0, double L1,
+                                      double L2, int natom, const double *RZ, double sigma, double *part)
+{
+    __shared__ double red[kEBlock];
+    const long long N = (long long)n0 * n1 * n2;
+    const double pi = 3.14159265358979323846;
+    const double norm = pow(2.0 * pi * sigma * sigma, -1.5), inv2s2 = 1.0 / (2.0 * sigma * sigma);
+    const double rs2 = 1.0 / (sqrt(2.0) * sigma), v0 = sqrt(2.0 / pi) / sigma;
+    double acc = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % n0), j = (int)((q / n0) % n1), k = (int)(q / ((long long)n0 * n1));
+        for (int J = 0; J < natom; J++) {
+            const double Z = RZ[4 * J + 3];
+            const double r2 = min_image_r2(i, j, k, h0, h1, h2, L0, L1, L2, RZ, J);
+            const double r = sqrt(r2);
+            const double V = r > 0.0 ? -Z * erf(r * rs2) / r : -Z * v0;
+            acc += -Z * norm * exp(-r2 * inv2s2) * V;
+        }
+    }
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// per-block sums of (eps_xc - V_xc) rho + (b - rho) phi / 2
+__global__ void k_free_energy_partial(long long n, const double *rho, const double *b, const double *phi, const double *exc,
+                                      const double *vxc, double *part)
+{
+    __shared__ double red[kEBlock];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += (exc[i] - vxc[i]) * rho[i] + 0.5 * (b[i] - rho[i]) * phi[i];
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// one block per atom J: f_J = -dV sum_q b_J^q (nabla_h phi)^q, the summation-by-parts form of
+// dV sum_q (nabla_h b_J)^q phi^q on the periodic grid
+__global__ void k_local_force(int n0, int n1, int n2, double h0, double h1, double h2, double L0, double L1, double L2,
+                              const double *RZ, double sigma, double dV, const double *gx, const double *gy,
+                              const double *gz, double *force)
+{
+    __shared__ double red[kEBlock];
+    const int J = blockIdx.x;
+    const long long N = (long long)n0 * n1 * n2;
+    const double norm = pow(2.0 * 3.14159265358979323846 * sigma * sigma, -1.5), inv2s2 = 1.0 / (2.0 * sigma * sigma);
+    const double Z = RZ[4 * J + 3];
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (long long q = threadIdx.x; q < N; q += blockDim.x) {
+        const int i = (int)(q % n0), j = (int)((q / n0) % n1), k = (int)(q / ((long long)n0 * n1));
+        const double bj = -Z * norm * exp(-min_image_r2(i, j, k, h0, h1, h2, L0, L1, L2, RZ, J) * inv2s2);
+        sx += bj * gx[q];
+        sy += bj * gy[q];
+        sz += bj * gz[q];
+    }
+    sx = block_sum(sx, red);
+    sy = block_sum(sy, red);
+    sz = block_sum(sz, red);
+    if (threadIdx.x == 0) {
+        force[3 * J] = -dV * sx;
+        force[3 * J + 1] = -dV * sy;
+        force[3 * J + 2] = -dV * sz;
+    }
+}
+
 int grid_of(long long n, int num_sms)
 {
     long long g = (n + kEBlock - 1) / kEBlock;
@@ -206,6 +320,42 @@ cudaError_t launch_lincomb(long long n, double alpha, const double *a, double be
 cudaError_t launch_add(long long n, const double *a, const double *b, double *out, int num_sms, cudaStream_t stream)
 {
     k_add<<<grid_of(n, num_sms), kEBlock, 0, stream>>>(n, a, b, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sq
+
+namespace sq {
+
+cudaError_t launch_grad_h(const int n[3], const GradWeights &gw, const double *v, double *g, int num_sms,
+                          cudaStream_t stream)
+{
+    const long long N = (long long)n[0] * n[1] * n[2];
+    k_grad_h<<<grid_of(N, num_sms), kEBlock, 0, stream>>>(n[0], n[1], n[2], gw, v, g, g + N, g + 2 * N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_self_energy_partial(const int n[3], const double h[3], const double L[3], int natom, const double *d_RZ,
+                                       double sigma, double *part, cudaStream_t stream)
+{
+    k_self_energy_partial<<<kDotBlocks, kEBlock, 0, stream>>>(n[0], n[1], n[2], h[0], h[1], h[2], L[0], L[1], L[2], natom,
+                                                              d_RZ, sigma, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_free_energy_partial(long long n, const double *rho, const double *b, const double *phi,
+                                       const double *exc, const double *vxc, double *part, cudaStream_t stream)
+{
+    k_free_energy_partial<<<kDotBlocks, kEBlock, 0, stream>>>(n, rho, b, phi, exc, vxc, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local_force(const int n[3], const double h[3], const double L[3], int natom, const double *d_RZ,
+                               double sigma, double dV, const double *g, double *d_force, cudaStream_t stream)
+{
+    const long long N = (long long)n[0] * n[1] * n[2];
+    k_local_force<<<natom, kEBlock, 0, stream>>>(n[0], n[1], n[2], h[0], h[1], h[2], L[0], L[1], L[2], d_RZ, sigma, dV, g,
+                                                 g + N, g + 2 * N, d_force);
     return cudaGetLastError();
 }
 

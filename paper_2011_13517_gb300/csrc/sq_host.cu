@@ -2834,3 +2834,114 @@ extern "C" sq_status sq_mixer_step(sq_mixer m, const double *d_vin, const double
     SQ_CUDA(cudaStreamSynchronize(stream));
     return SQ_OK;
 }
+
+// ------------------------------------------------------------------------------------------------
+// Discrete free energy and local force (Sec. 3 "Free energy" and "Atomic forces")
+
+namespace {
+
+sq_status upload_atoms(int natom, const double *R, const double *Z, DevBuf &d_rz, cudaStream_t stream)
+{
+    std::vector<double> rz(4 * (size_t)std::max(natom, 1), 0.0);
+    for (int J = 0; J < natom; J++) {
+        for (int a = 0; a < 3; a++) rz[4 * J + a] = R[3 * J + a];
+        rz[4 * J + 3] = Z[J];
+        for (int a = 0; a < 4; a++)
+            if (!std::isfinite(rz[4 * J + a])) return fail(SQ_ERR_NOT_FINITE, "atom %d", J);
+    }
+    SQ_CUDA(cudaMalloc(&d_rz.p, sizeof(double) * rz.size()));
+    SQ_CUDA(cudaMemcpyAsync(d_rz.p, rz.data(), sizeof(double) * rz.size(), cudaMemcpyHostToDevice, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    return SQ_OK;
+}
+
+sq_status sum_partials(const double *d_part, cudaStream_t stream, double *out)
+{
+    double part[kDotBlocks];
+    SQ_CUDA(cudaMemcpyAsync(part, d_part, sizeof(part), cudaMemcpyDeviceToHost, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    double s = 0.0;
+    for (int i = 0; i < kDotBlocks; i++) s += part[i];
+    *out = s;
+    return SQ_OK;
+}
+
+}  // namespace
+
+extern "C" sq_status sq_self_energy(const int n[3], const double box[3], int natom, const double *R, const double *Z,
+                                    double sigma_b, double *E_self, void *stream_)
+{
+    g_last_error[0] = 0;
+    sq_status s;
+    if ((s = check_grid(n, box))) return s;
+    if (!E_self || natom < 0 || (natom > 0 && (!R || !Z))) return fail(SQ_ERR_ARG, "null argument or natom = %d", natom);
+    if (!(sigma_b > 0) || !std::isfinite(sigma_b)) return fail(SQ_ERR_ARG, "sigma_b = %g", sigma_b);
+    *E_self = 0.0;
+    if (natom == 0) return SQ_OK;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    DevBuf d_rz, part;
+    if ((s = upload_atoms(natom, R, Z, d_rz, stream))) return s;
+    SQ_CUDA(cudaMalloc(&part.p, sizeof(double) * kDotBlocks));
+    const double h[3] = {box[0] / n[0], box[1] / n[1], box[2] / n[2]};
+    SQ_COUNT(1);
+    SQ_CUDA(sq::launch_self_energy_partial(n, h, box, natom, d_rz.p, sigma_b, part.p, stream));
+    double t = 0.0;
+    if ((s = sum_partials(part.p, stream, &t))) return s;
+    *E_self = -0.5 * h[0] * h[1] * h[2] * t;
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_free_energy(const int n[3], const double box[3], const double *d_rho, const double *d_b,
+                                    const double *d_phi, const double *d_exc, const double *d_vxc, double F_band,
+                                    double E_self, double *F, void *stream_)
+{
+    g_last_error[0] = 0;
+    sq_status s;
+    if ((s = check_grid(n, box))) return s;
+    if (!d_rho || !d_b || !d_phi || !d_exc || !d_vxc || !F) return fail(SQ_ERR_ARG, "null argument");
+    if (!std::isfinite(F_band) || !std::isfinite(E_self)) return fail(SQ_ERR_NOT_FINITE, "F_band or E_self");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const long long N = (long long)n[0] * n[1] * n[2];
+    DevBuf part;
+    SQ_CUDA(cudaMalloc(&part.p, sizeof(double) * kDotBlocks));
+    SQ_COUNT(1);
+    SQ_CUDA(sq::launch_free_energy_partial(N, d_rho, d_b, d_phi, d_exc, d_vxc, part.p, stream));
+    double t = 0.0;
+    if ((s = sum_partials(part.p, stream, &t))) return s;
+    const double dV = (box[0] / n[0]) * (box[1] / n[1]) * (box[2] / n[2]);
+    *F = F_band + dV * t + E_self;
+    if (!std::isfinite(*F)) return fail(SQ_ERR_NOT_FINITE, "free energy");
+    return SQ_OK;
+}
+
+extern "C" sq_status sq_local_force(const int n[3], const double box[3], int fd_order, int natom, const double *R,
+                                    const double *Z, double sigma_b, const double *d_phi, double *force,
+                                    void *stream_)
+{
+    g_last_error[0] = 0;
+    sq_status s;
+    if ((s = check_grid(n, box))) return s;
+    if (fd_order < 2 || fd_order > 2 * kMaxHalfWidth || fd_order % 2) return fail(SQ_ERR_ARG, "fd_order %d", fd_order);
+    if (!d_phi || !force || natom < 0 || (natom > 0 && (!R || !Z))) return fail(SQ_ERR_ARG, "null argument or natom");
+    if (!(sigma_b > 0) || !std::isfinite(sigma_b)) return fail(SQ_ERR_ARG, "sigma_b = %g", sigma_b);
+    if (natom == 0) return SQ_OK;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const long long N = (long long)n[0] * n[1] * n[2];
+    const double h[3] = {box[0] / n[0], box[1] / n[1], box[2] / n[2]};
+    sq::GradWeights gw;
+    memset(&gw, 0, sizeof(gw));
+    const Fd1Weights w1 = fd1_coefficients(fd_order);
+    gw.p = w1.p;
+    for (int a = 0; a < 3; a++)
+        for (int d = 1; d <= w1.p; d++) gw.a[a][d] = w1.a[d] / h[a];
+    DevBuf d_rz, g, d_f;
+    if ((s = upload_atoms(natom, R, Z, d_rz, stream))) return s;
+    SQ_CUDA(cudaMalloc(&g.p, sizeof(double) * 3 * (size_t)N));
+    SQ_CUDA(cudaMalloc(&d_f.p, sizeof(double) * 3 * (size_t)natom));
+    SQ_COUNT(2);
+    SQ_CUDA(sq::launch_grad_h(n, gw, d_phi, g.p, current_sms(), stream));
+    SQ_CUDA(sq::launch_local_force(n, h, box, natom, d_rz.p, sigma_b, h[0] * h[1] * h[2], g.p, d_f.p, stream));
+    SQ_CUDA(cudaMemcpyAsync(force, d_f.p, sizeof(double) * 3 * (size_t)natom, cudaMemcpyDeviceToHost, stream));
+    SQ_CUDA(cudaStreamSynchronize(stream));
+    return SQ_OK;
+}

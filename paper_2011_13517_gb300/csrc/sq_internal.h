@@ -151,7 +151,12 @@ struct LapWeights {
     int p;
     double c[3][kMaxHalfWidth + 1];
 };
-constexpr int kDotBlocks = 256;   // partial sums written by launch_dot_partial
+// GradWeights: a[a][d] = first-derivative FD weight a_d / h_a along axis a, d = 1..p.
+struct GradWeights {
+    int p;
+    double a[3][kMaxHalfWidth + 1];
+};
+constexpr int kDotBlocks = 256;   // partial sums written by launch_dot_partial and the *_partial launchers
 cudaError_t launch_lda_pw92(long long n, const double *rho, double *exc, double *vxc, int num_sms, cudaStream_t stream);
 // d_RZ: device [natom][4] = (x, y, z, Z)
 cudaError_t launch_pseudocharge(const int n[3], const double h[3], const double L[3], int natom, const double *d_RZ,
@@ -167,5 +172,15 @@ cudaError_t launch_cg_dir(long long n, double beta, const double *r, double *p, 
 cudaError_t launch_add(long long n, const double *a, const double *b, double *out, int num_sms, cudaStream_t stream);
 cudaError_t launch_lincomb(long long n, double alpha, const double *a, double beta, const double *b, double *out,
                            int num_sms, cudaStream_t stream);
+// g: device [3][N] (x, y, z components)
+cudaError_t launch_grad_h(const int n[3], const GradWeights &gw, const double *v, double *g, int num_sms,
+                          cudaStream_t stream);
+cudaError_t launch_self_energy_partial(const int n[3], const double h[3], const double L[3], int natom, const double *d_RZ,
+                                       double sigma, double *part, cudaStream_t stream);
+cudaError_t launch_free_energy_partial(long long n, const double *rho, const double *b, const double *phi,
+                                       const double *exc, const double *vxc, double *part, cudaStream_t stream);
+// one block per atom; d_force: device [natom][3]
+cudaError_t launch_local_force(const int n[3], const double h[3], const double L[3], int natom, const double *d_RZ,
+                               double sigma, double dV, const double *g, double *d_force, cudaStream_t stream);
 
 }  // namespace sq

@@ -35,7 +35,8 @@ EXPORTS = ["sq_build_hamiltonian", "sq_density", "sq_fermi_level", "sq_fermi_wei
            "sq_kernel_launches", "sq_fma_throughput", "sq_mma_throughput", "sq_moments_noalloc", "sq_batch_create", "sq_batch_density",
            "sq_batch_info", "sq_batch_destroy", "sq_density_vjp", "sq_kernel_name", "sq_destroy",
            "sq_status_string", "sq_last_error", "sq_lda_pw92", "sq_pseudocharge", "sq_poisson_periodic",
-           "sq_effective_potential", "sq_mixer_create", "sq_mixer_step", "sq_mixer_destroy"]
+           "sq_effective_potential", "sq_mixer_create", "sq_mixer_step", "sq_mixer_destroy", "sq_self_energy",
+           "sq_free_energy", "sq_local_force"]
 
 
 class SQError(RuntimeError):
@@ -371,6 +372,48 @@ def sq_mixer_step(m: Mixer, d_vin, d_vout, d_vnext, stream=None):
 
 def sq_mixer_destroy(m: Mixer):
     m.close()
+
+
+def _atoms(R, Z):
+    R = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(-1, 3))
+    Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64).reshape(-1))
+    if R.shape[0] != Z.size:
+        raise ValueError("R and Z disagree on the atom count")
+    return R, Z
+
+
+def sq_self_energy(n, box, R, Z, sigma_b, stream=None):
+    """sq_self_energy: E_self^h of the Gaussian pseudocharges."""
+    gn, gb = _grid(n, box)
+    R, Z = _atoms(R, Z)
+    e = ctypes.c_double()
+    _check(lib().sq_self_energy(gn, gb, ctypes.c_int(Z.size), R.ctypes.data_as(ctypes.c_void_p),
+                                Z.ctypes.data_as(ctypes.c_void_p), ctypes.c_double(sigma_b), ctypes.byref(e),
+                                _stream(stream)))
+    return e.value
+
+
+def sq_free_energy(n, box, d_rho, d_b, d_phi, d_exc, d_vxc, F_band, E_self, stream=None):
+    """sq_free_energy: the discrete free energy F^h."""
+    gn, gb = _grid(n, box)
+    N = int(np.prod([int(v) for v in n]))
+    F = ctypes.c_double()
+    _check(lib().sq_free_energy(gn, gb, *[_dev_ptr(t, numel=N) for t in (d_rho, d_b, d_phi, d_exc, d_vxc)],
+                                ctypes.c_double(F_band), ctypes.c_double(E_self), ctypes.byref(F), _stream(stream)))
+    return F.value
+
+
+def sq_local_force(n, box, fd_order, R, Z, sigma_b, d_phi, stream=None):
+    """sq_local_force: [natom, 3] local pseudopotential forces."""
+    gn, gb = _grid(n, box)
+    R, Z = _atoms(R, Z)
+    N = int(np.prod([int(v) for v in n]))
+    f = np.zeros((Z.size, 3))
+    _check(lib().sq_local_force(gn, gb, ctypes.c_int(fd_order), ctypes.c_int(Z.size),
+                                R.ctypes.data_as(ctypes.c_void_p), Z.ctypes.data_as(ctypes.c_void_p),
+                                ctypes.c_double(sigma_b), _dev_ptr(d_phi, numel=N),
+                                f.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return f
 
 
 def sq_energy(h: Handle, stream=None):

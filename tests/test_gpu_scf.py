@@ -141,3 +141,31 @@ def test_scf_tiny_cell_matches_oracle():
     np.testing.assert_allclose(v_it, ref["veff"], rtol=0, atol=1e-8 * np.abs(ref["veff"]).max())
     np.testing.assert_allclose(rho_it, ref["rho"], rtol=0, atol=1e-8 * np.abs(ref["rho"]).max())
     assert abs(lam - ref["lam_f"]) < 1e-8
+
+
+@pytest.mark.parametrize("make", [cells.tiny_cell, cells.vacancy_cell])
+def test_free_energy_and_local_force_match_oracle(make):
+    """E_self^h, the density terms of F^h (Eq. DiscreteEnergy) and the local force (Eq.
+    DiscreteLocalForce; the GPU sums b_J against nabla_h phi, the oracle nabla_h b_J against phi) on a
+    fixed smooth density of the cell's electron count: E_self to 1e-12 relative, F^h to the Poisson
+    tolerance, forces to the same bound relative to the largest component."""
+    c = make()
+    rho = np.exp(-c.veff.reshape(-1))
+    rho *= c.N_e / (rho.sum() * float(np.prod(c.h)))
+    Z = es.valence_charges(c)
+    b = torch.empty(c.N_d, dtype=torch.float64, device="cuda")
+    sq.sq_pseudocharge(c.n, c.box, c.R, Z, SIGMA_B, b)
+    phi, exc, vxc, veff = [torch.empty(c.N_d, dtype=torch.float64, device="cuda") for _ in range(4)]
+    d_rho = dev(rho)
+    sq.sq_effective_potential(c.n, c.box, c.fd_order, d_rho, b, phi, exc, vxc, veff, tol=1e-13)
+    e_self = sq.sq_self_energy(c.n, c.box, c.R, Z, SIGMA_B)
+    e_ref = es.self_energy_discrete(c, SIGMA_B)
+    assert abs(e_self - e_ref) < 1e-12 * abs(e_ref)
+    F = sq.sq_free_energy(c.n, c.box, d_rho, b, phi, exc, vxc, 0.0, e_self)
+    F_ref, _ = es.free_energy(c, SIGMA_B, rho, 0.0, 0.0, c.kT)
+    lam = np.abs(es.laplacian_symbol(c)).reshape(-1)
+    tol = 10.0 * lam.max() / lam[lam > 0].min() * 1e-13
+    assert abs(F - F_ref) < 1e-9 * abs(F_ref) + tol * abs(F_ref), (F, F_ref)
+    f = sq.sq_local_force(c.n, c.box, c.fd_order, c.R, Z, SIGMA_B, phi)
+    f_ref = es.local_force(c, SIGMA_B, es.poisson_periodic(rho + es.pseudocharge(c, SIGMA_B), c))
+    np.testing.assert_allclose(f, f_ref, rtol=0, atol=1e-9 * np.abs(f_ref).max() + tol * np.abs(f_ref).max())

@@ -141,3 +141,45 @@ def test_scf_fixed_point_is_self_consistent_and_independent_of_the_mixing():
     vout, _, _, _ = es.effective_potential(r1["rho"], c, 1.0)
     assert np.linalg.norm(vout - r1["veff"]) <= 1e-10 * np.linalg.norm(vout)
     assert abs(r1["rho"].sum() * float(np.prod(c.h)) - c.N_e) < 1e-9 * c.N_e
+
+
+def test_local_force_is_minus_the_derivative_of_the_electrostatic_energy():
+    """At a fixed density the local force f_J = dV sum (nabla_h b_J) phi (Eq. DiscreteLocalForce) is
+    -dE/dR_J of the discrete electrostatic energy E = dV/2 sum (rho + b) phi + E_self^h (phi of rho + b),
+    the pseudocharge b_J moving with its nucleus: central differences in R_J (95-atom cell, where the
+    Gaussians are far inside the minimum image)."""
+    import copy
+    c = cells.vacancy_cell()
+    sig = 1.0
+    rho = np.exp(-c.veff.reshape(-1))
+    rho *= c.N_e / (rho.sum() * float(np.prod(c.h)))
+    dV = float(np.prod(c.h))
+
+    def energy(cc):
+        b = es.pseudocharge(cc, sig)
+        phi = es.poisson_periodic(rho + b, cc)
+        return 0.5 * dV * float(np.sum((rho + b) * phi)) + es.self_energy_discrete(cc, sig), phi
+
+    _, phi = energy(c)
+    f = es.local_force(c, sig, phi)
+    J, e = 7, 1e-3
+    for d in range(3):
+        cp, cm = copy.deepcopy(c), copy.deepcopy(c)
+        cp.R[J, d] += e
+        cm.R[J, d] -= e
+        fd = -(energy(cp)[0] - energy(cm)[0]) / (2 * e)
+        assert abs(f[J, d] - fd) < 1e-6 * np.abs(f).max(), (d, f[J, d], fd)
+    # summation by parts on the periodic grid: sum (D b_J) phi = -sum b_J (D phi)
+    shape = (int(c.n[2]), int(c.n[1]), int(c.n[0]))
+    g = es.grad_h(phi.reshape(shape), c)
+    Z = es.valence_charges(c)
+    bJ = es.pseudocharge_one(c, sig, J, Z[J])
+    sbp = np.array([-dV * float(np.sum(bJ * g[d])) for d in range(3)])
+    np.testing.assert_allclose(f[J], sbp, rtol=0, atol=1e-13 * np.abs(f).max())
+
+
+def test_discrete_self_energy_of_the_cell():
+    c = cells.vacancy_cell()
+    Z = es.valence_charges(c)
+    e = es.self_energy_discrete(c, 1.0)
+    assert abs(e - es.self_energy_continuum(Z, 1.0)) < 1e-6 * abs(e)
