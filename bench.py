@@ -427,6 +427,55 @@ def run_gauss(args, sq, torch, world, rank, barrier, dist):
                           "results": {"lambda_f": lam, "U": U, "S": S}, "clocks": clk.summary()}), flush=True)
 
 
+def run_scf(args, sq, torch, world, rank, barrier, dist):
+    """The SCF loop of the vacancy cell (Sec. 3 flow): per iteration the build of V_in, the SQ density
+    (FP32 unless --precision fp64), the effective potential (pseudocharges, Poisson, LDA) and an Anderson
+    step (beta 0.3, history 5), until |V_out - V_in| / |V_out| <= 1e-6 or 40 iterations.  One step of
+    this workload is one SCF iteration."""
+    precision = sq.SQ_FP64 if args.precision == "fp64" else sq.SQ_FP32
+    c = cells.vacancy_cell()
+    if args.profile:
+        c.K = 8
+    N, sig = c.N_d, 1.0
+    Z = np.array([float(cells.VALENCE[int(t)]) for t in c.species])
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    sq.sq_pseudocharge(c.n, c.box, c.R, Z, sig, b)
+    v_in = torch.from_numpy(np.ascontiguousarray(c.veff.reshape(-1))).cuda()
+    rho, phi, exc, vxc, v_out = [torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(5)]
+    mixer = sq.sq_mixer_create(N, history=5, beta=0.3)
+    stream = torch.cuda.current_stream()
+
+    def iteration():
+        h = sq.build_for_cell(c, d_veff=v_in)
+        sq.sq_density(h, c.K, c.kT, c.N_e, precision, 0, rho)
+        h.close()
+        sq.sq_effective_potential(c.n, c.box, c.fd_order, rho, b, phi, exc, vxc, v_out, tol=1e-10)
+        return sq.sq_mixer_step(mixer, v_in, v_out, v_in)
+
+    errs = [iteration() for _ in range(max(args.warmup, 3))]
+    times = []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            errs.append(iteration())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    mixer.close()
+    ms = statistics.mean(times)
+    if rank == 0:
+        print(json.dumps({"metric": "SCF iterations (SQ density + effective potential + mixing) grid-points/sec",
+                          "value": world * N / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                          "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision else "f64",
+                          "data": "synthetic", "config": dict(workload_config(c), mixing="Anderson, beta 0.3, history 5",
+                                                              pseudocharge_sigma=sig),
+                          "scf_errors": errs, "clocks": clk.summary()}), flush=True)
+
+
 def golden_errors(cell, lam, U, S, rho, force):
     """Errors of one result against the FP64 oracle's golden values of the same cell (written by
     tests/golden/make_golden.py): the rho error stated beside each throughput number."""
@@ -460,11 +509,11 @@ def main():
     ap.add_argument("--no-vacancy", action="store_true", help="skip the extra vacancy-cell line")
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed steps of the secondary FP64 measurement (0: same as --steps)")
-    ap.add_argument("--workload", choices=["precision", "vacancy", "batch", "adjoint", "gauss"], default="precision",
+    ap.add_argument("--workload", choices=["precision", "vacancy", "batch", "adjoint", "gauss", "scf"], default="precision",
                     help="precision: the headline line (286-atom cell, 29^3 cubes, K=80); vacancy: the 95-atom "
                          "cell alone; batch: 32 defect cells in one graph-captured batch; adjoint: the "
                          "reverse-mode derivative of the vacancy cell; gauss: Gauss (Lanczos) quadrature on "
-                         "the vacancy cell")
+                         "the vacancy cell; scf: SCF iterations of the vacancy cell")
     ap.add_argument("--kb", choices=["mma", "fma"], default="mma",
                     help="projector term of the FP32 cluster kernel (29^3 cubes): tensor cores (3xTF32 warp MMAs) "
                          "or CUDA-core FMAs (SQ_KB_FMA)")
@@ -501,6 +550,9 @@ def main():
         return
     if args.workload == "gauss":
         run_gauss(args, sq, torch, world, rank, barrier, dist)
+        return
+    if args.workload == "scf":
+        run_scf(args, sq, torch, world, rank, barrier, dist)
         return
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
