@@ -138,3 +138,25 @@ def test_scf_entry_points_reject_bad_arguments_before_any_launch():
                                      ctypes.c_void_p(8), ctypes.byref(it), ctypes.byref(res), null) == 1
     assert L.sq_effective_potential(n, box, 12, null, null, ctypes.c_double(1e-10), 10, null, null, null, null,
                                     ctypes.byref(it), ctypes.byref(res), null) == 1
+
+
+def test_mixer_and_energy_entry_points_reject_bad_arguments_on_the_host():
+    """sq_mixer_create, sq_self_energy, sq_free_energy and sq_local_force validate their arguments
+    before any device work (this runs without a GPU)."""
+    import ctypes
+    L = sq.lib()
+    out = ctypes.c_void_p()
+    for n, hist, beta in ((0, 5, 0.3), (10, -1, 0.3), (10, 33, 0.3), (10, 5, 0.0), (10, 5, 1.5)):
+        assert L.sq_mixer_create(ctypes.c_longlong(n), hist, ctypes.c_double(beta), ctypes.byref(out)) == 1
+    n3 = (ctypes.c_int * 3)(8, 8, 8)
+    box = (ctypes.c_double * 3)(4.0, 4.0, 4.0)
+    null = ctypes.c_void_p(0)
+    e = ctypes.c_double()
+    assert L.sq_self_energy(n3, box, 2, null, null, ctypes.c_double(1.0), ctypes.byref(e), null) == 1
+    assert L.sq_self_energy(n3, box, 0, null, null, ctypes.c_double(0.0), ctypes.byref(e), null) == 1
+    # no atoms: zero self energy without device work
+    assert L.sq_self_energy(n3, box, 0, null, null, ctypes.c_double(1.0), ctypes.byref(e), null) == 0 and e.value == 0.0
+    assert L.sq_free_energy(n3, box, null, null, null, null, null, ctypes.c_double(0.0), ctypes.c_double(0.0),
+                            ctypes.byref(e), null) == 1
+    f = (ctypes.c_double * 3)()
+    assert L.sq_local_force(n3, box, 5, 1, null, null, ctypes.c_double(1.0), ctypes.c_void_p(8), f, null) == 1
